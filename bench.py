@@ -1,0 +1,333 @@
+#!/usr/bin/env python
+"""Benchmark of the reverse k-MIPS top-N hot path on one GB300 (or N replicas).
+
+One step = one rkm_topn call on the MF-like workload users n=500,000, items m=100,000,
+d=64, k=25, N=50 (FP32 grid inputs, resident in HBM): prep, thresholds (product +
+selector + exact rescoring), Eq. 2 bounds, filtered counting, band rescoring, top-N.
+
+metric: user-item pairs scored per second = n*m / step time (the dense pair count of
+the problem, whatever the filter skips).  L2 is flushed (a 512 MiB write) before each
+timed step, outside the timed events.
+
+--impl reference times the FP64 oracle on the host cores on a bounded user sample of
+the same workload (the CPU baseline; the paper has no GPU implementation).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "user-item pairs scored/sec (end-to-end top-N)"
+UNIT = "pairs/s"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--precision", default="bf16", choices=["bf16", "fp32"])
+    ap.add_argument("--workload", default="mf-500k")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    return ap.parse_args()
+
+
+def dist_init():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        os.environ.setdefault("MASTER_ADDR", "127.0.0.1")
+        dist.init_process_group("gloo", rank=rank, world_size=world)
+    return rank, local, world
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(x: float, world: int) -> float:
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms while running."""
+
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines: list[str] = []
+        self.reader = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.QUERY}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.reader = threading.Thread(target=self._read, daemon=True)
+            self.reader.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for name, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def measured_peaks() -> dict:
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            p = json.load(f)
+        p["source"] = "measured"
+        return p
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0, "sm_max_mhz": 2070.0,
+            "source": "fallback"}
+
+
+def fp32_alu_peak_tflops(sm_mhz: float, sms: int = 152) -> float:
+    # 128 FP32 FMA lanes per SM, 2 FLOP per FMA.
+    return sms * 128 * 2 * sm_mhz * 1e6 / 1e12
+
+
+def cpu_baseline(W, workload: str, seconds: float) -> dict:
+    """The oracle as it stands on the host cores, on users [0, S) of the workload against
+    every item (Definition 1 thresholds and the histogram of S_k(u)), S grown in blocks
+    until about `seconds` of work.  Runs in a spawned child so BLAS threads are pinned."""
+    import multiprocessing as mp
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    p = ctx.Process(target=_cpu_child, args=(workload, W.k, seconds, q))
+    p.start()
+    res = q.get()
+    p.join()
+    return res
+
+
+def _cpu_child(cfg, k, seconds, q):
+    threads = os.cpu_count() or 1
+    os.environ["OPENBLAS_NUM_THREADS"] = "1"
+    os.environ["OMP_NUM_THREADS"] = "1"
+    os.environ["MKL_NUM_THREADS"] = "1"
+    sys.path.insert(0, ROOT)
+    import numpy as np  # noqa: F401
+    import oracle
+    import workloads
+    W = workloads.make(cfg)
+    block = 64 * threads
+    t0 = time.perf_counter()
+    done = 0
+    while True:
+        u1 = min(W.n, done + block)
+        tau, tid, topk = oracle.kmips(W.U[done:u1], W.P, k, block=64, threads=threads)
+        oracle.scores_histogram(topk, W.m)
+        done = u1
+        if time.perf_counter() - t0 >= seconds or done >= W.n:
+            break
+    dt = time.perf_counter() - t0
+    q.put({"value": done * W.m / dt, "unit": UNIT, "cores": threads, "kind": "oracle",
+           "sample": f"users [0,{done}) x all {W.m} items of {cfg}: FP64 thresholds + histogram, {dt:.1f} s"})
+
+
+def run_reference(args, rank, world):
+    """The FP64 oracle on the host cores: each step is a bounded user sample."""
+    if rank != 0:
+        return
+    import oracle
+    import workloads
+    threads = os.cpu_count() or 1
+    W = workloads.make(args.workload)
+    sample = 32 * threads
+    times = []
+    for step in range(args.warmup + args.steps):
+        u0 = (step * sample) % max(1, W.n - sample)
+        t0 = time.perf_counter()
+        tau, tid, topk = oracle.kmips(W.U[u0:u0 + sample], W.P, W.k, block=32, threads=threads)
+        oracle.scores_histogram(topk, W.m)
+        dt = time.perf_counter() - t0
+        if step >= args.warmup:
+            times.append(dt)
+    ms = 1000 * statistics.mean(times)
+    value = sample * W.m / (ms / 1000)
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": args.workload, "n": W.n, "m": W.m, "d": W.d, "k": W.k, "N": W.N,
+                       "sample_users_per_step": sample},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
+                             "sample": f"{sample} users x all {W.m} items per step (FP64 thresholds + histogram)"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args, rank, local, world):
+    import numpy as np
+    import torch
+
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_2504_13445_gb300 as rkm
+    import workloads
+
+    torch.cuda.set_device(local)
+    W = workloads.make(args.workload)
+    U = torch.from_numpy(W.U).cuda()
+    P = torch.from_numpy(W.P).cuda()
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device="cuda")
+    ctx = rkm.Context(args.precision, device=local, profile=True)
+    for _ in range(args.warmup):
+        ctx.topn(U, P, W.k, W.N)
+    torch.cuda.synchronize()
+    stream = torch.cuda.current_stream()
+    clocks = ClockSampler(local)
+    barrier(world)
+    clocks.start()
+    torch.cuda.synchronize()
+    step_ms, thr_ms, thr_launch, launches, counted, cand, band = [], [], [], 0, [], [], []
+    for _ in range(args.steps):
+        flush.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        ids, tops = ctx.topn(U, P, W.k, W.N)
+        e1.record(stream)
+        e1.synchronize()
+        step_ms.append(e0.elapsed_time(e1))
+        st = ctx.stats()
+        thr_ms.append(st["phase_ms"]["threshold"])
+        thr_launch.append(st["threshold_launches"])
+        launches += st["kernel_launches"]
+        counted.append(st["items_counted"])
+        cand.append(st["candidates"])
+        band.append(st["band_pairs"])
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    barrier(world)
+    total_ms = max_over_ranks(sum(step_ms), world)
+    ms = total_ms / args.steps
+    pairs = W.n * W.m
+    value = world * pairs / (ms / 1000)
+
+    # End to end through the host-buffer entry point: pinned host inputs, copies inside.
+    e2e = None
+    if not args.no_e2e:
+        Uh = torch.from_numpy(W.U).pin_memory()
+        Ph = torch.from_numpy(W.P).pin_memory()
+        Un, Pn = Uh.numpy(), Ph.numpy()
+        ctx.topn_host(Un, Pn, W.k, W.N)
+        torch.cuda.synchronize()
+        ts = []
+        for _ in range(max(3, args.steps // 2)):
+            t0 = time.perf_counter()
+            ctx.topn_host(Un, Pn, W.k, W.N)
+            ts.append(time.perf_counter() - t0)
+        e2e_s = max_over_ranks(statistics.mean(ts), world)
+        e2e = {"value": world * pairs / e2e_s, "unit": UNIT, "ms_per_step": 1000 * e2e_s,
+               "h2d_bytes_per_step": int(W.U.nbytes + W.P.nbytes), "d2h_bytes_per_step": int(8 * W.N),
+               "api": "rkm_topn_host"}
+
+    if rank != 0:
+        return
+    peaks = measured_peaks()
+    thr_avg = statistics.mean(t / max(1, l) for t, l in zip(thr_ms, thr_launch))
+    flops = 2.0 * W.n * W.m * W.d
+    achieved = flops / (thr_avg / 1000) / 1e12
+    if args.precision == "bf16":
+        peak = peaks["bf16_tflops"]
+        roof = {"bound": "tensor", "kernel": "k_threshold_tc (threshold product + selector)",
+                "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                "traffic": None, "peak_source": f"{peaks['source']} bf16_tflops (burst)"}
+    else:
+        sm_mhz = peaks.get("sm_max_mhz", 2070.0)
+        peak = fp32_alu_peak_tflops(sm_mhz)
+        roof = {"bound": "alu", "kernel": "k_threshold_simt (threshold product + selector)",
+                "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                "traffic": None, "peak_source": f"152 SMs x 128 FP32 FMA/clk x 2 x {sm_mhz:.0f} MHz"}
+    roof["kernel_ms"] = thr_avg
+    roof["algorithmic_flops_per_launch"] = flops
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "bf16" if args.precision == "bf16" else "f32",
+            "data": "synthetic",
+            "config": {"workload": args.workload, "n": W.n, "m": W.m, "d": W.d, "k": W.k, "N": W.N,
+                       "precision": args.precision, "inputs": "FP32 on the 2^-12 grid, MF-like",
+                       "l2": "flushed (512 MiB write) before each timed step",
+                       "parallelism": "replicas" if world > 1 else "single GPU"},
+            "roofline": roof,
+            "gpu_launches": int(launches),
+            "clocks": clk,
+            "detail": {"items_counted_mean": statistics.mean(counted), "candidates_mean": statistics.mean(cand),
+                       "band_pairs_mean": statistics.mean(band), "phase_ms_last_step": st["phase_ms"]}}
+    if e2e:
+        line["e2e"] = e2e
+    if not args.no_cpu_baseline and world == 1:
+        line["cpu_baseline"] = cpu_baseline(W, args.workload, args.cpu_seconds)
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    rank, local, world = dist_init()
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+    else:
+        run_ours(args, rank, local, world)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,202 @@
+/*
+ * rkm.h -- C ABI of the GB300 reverse k-MIPS top-N library (librkm.so).
+ *
+ * Problem (Amagata et al., "How to Mine Potentially Popular Items? A Reverse
+ * MIPS-based Approach", arXiv 2504.13445, Section 2.1):
+ *   users U (n x d), items P (m x d); item id = row index of P.
+ *   Definition 1 (k-MIPS): S_k(u) = the k items with the largest u.p.
+ *   Definition 2 / Eq. 1 (reverse k-MIPS): T_k(p) = {u : p in S_k(u)}.
+ *   Definition 3: the N items with the largest score(p) = |T_k(p)|.
+ * The paper breaks ties "arbitrarily"; this library fixes the order
+ *   i before j for user u  <=>  u.p_i > u.p_j  or  (u.p_i == u.p_j and i < j)
+ * for S_k(u), and "larger score, then smaller id" for the top N.  With t_u the
+ * k-th item of u under that order and tau_u = u.p_{t_u}:
+ *   i in S_k(u)  <=>  u.p_i > tau_u  or  (u.p_i == tau_u and i <= t_u).
+ *
+ * Exactness: tau_u is the FP64 value of u.p_{t_u}.  For inputs on the grid
+ * 2^e * q / 4096 (integer |q| <= 4096, one exponent e per row) that value is
+ * exact and every output below is bit-identical to exact arithmetic.  For
+ * other FP32 inputs inner products are evaluated as a left-to-right FP64 sum
+ * of exact FP64 products, and membership is decided on that value.
+ *
+ * Conventions shared by every entry point:
+ *  - Matrices are row-major FP32; `ld*` is the row stride in elements (>= d)
+ *    and must keep every row 4-byte aligned.
+ *  - Pointers marked "device" are CUDA device pointers owned by the caller;
+ *    the library reads or writes them only during the call.  Pointers marked
+ *    "host" are ordinary host memory.
+ *  - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *    stream).  Every call enqueues its kernels on that stream and returns
+ *    after its results are complete (each call reads back a device status
+ *    word, so it synchronises `stream` once, or twice after a retry).
+ *  - The context owns its scratch memory (device workspace grown on demand
+ *    and kept until rkm_destroy).  A context is not thread-safe: use one
+ *    context per host thread; distinct contexts are independent.
+ *  - Errors never trap on the device.  A call returns a status code and
+ *    rkm_last_error() describes it.  On error the outputs are unspecified.
+ */
+#ifndef RKM_H
+#define RKM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define RKM_API __attribute__((visibility("default")))
+#else
+#define RKM_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct rkm_ctx rkm_ctx;
+
+typedef enum {
+    RKM_OK = 0,
+    RKM_EINVAL = 1,     /* bad argument (null pointer, size, k, N, ld)          */
+    RKM_ENOMEM = 2,     /* device workspace allocation failed                   */
+    RKM_ECUDA = 3,      /* a CUDA runtime call or kernel launch failed          */
+    RKM_EOVERFLOW = 4,  /* a candidate or band buffer overflowed after retries  */
+    RKM_ETIMEOUT = 5,   /* a bounded device wait gave up                        */
+    RKM_ESTATE = 6,     /* call out of order (e.g. query before resident set)   */
+    RKM_EINTERNAL = 7   /* a device-side consistency check failed               */
+} rkm_status;
+
+typedef enum {
+    RKM_FP32 = 0,  /* FP32 CUDA-core products, FP64/integer exact rescoring       */
+    RKM_BF16 = 1,  /* BF16 tensor-core (tcgen05) products, FP32 accumulate,
+                      guard band + exact rescoring                               */
+    RKM_FP8 = 2    /* reserved: FP8 e4m3 products (not built; returns RKM_EINVAL) */
+} rkm_precision;
+
+typedef struct {
+    rkm_precision precision; /* default RKM_BF16                                   */
+    int k_max;               /* largest k accepted; default and maximum 64        */
+    int cand_capacity;       /* initial per-user candidate capacity (0 = auto)     */
+    int64_t band_capacity;   /* initial band-queue capacity in pairs (0 = auto)    */
+    int filter;              /* rkm_topn: 1 = Eq. 2 item filter (default), 0 = off */
+    int profile;             /* 1 = time each phase with CUDA events (rkm_stats)   */
+} rkm_opts;
+
+/* Phases timed when rkm_opts.profile is set (indices of rkm_stats.phase_ms). */
+enum {
+    RKM_PHASE_PREP = 0,      /* K1: norms, grid codes, item sort, operand packs    */
+    RKM_PHASE_THRESHOLD = 1, /* K2: threshold product + per-user selector          */
+    RKM_PHASE_EXACT = 2,     /* K3: exact tau_u / t_u from the candidates          */
+    RKM_PHASE_BOUNDS = 3,    /* K4: ratios tau_u/||u||, user bucket sort, packs    */
+    RKM_PHASE_COUNT = 4,     /* K5: counting product + classification              */
+    RKM_PHASE_BAND = 5,      /* K6: exact rescoring of band pairs                  */
+    RKM_PHASE_TOPN = 6,      /* K7: top-N select and the filter cut                */
+    RKM_PHASES = 8
+};
+
+typedef struct {
+    uint64_t pairs_total;       /* n*m (thresholds) plus n*m or n*q (counting)   */
+    uint64_t pairs_evaluated;   /* user-item products actually computed           */
+    uint64_t candidates;        /* threshold-pass candidates rescored exactly     */
+    uint64_t band_pairs;        /* counting-pass pairs rescored exactly           */
+    uint64_t items_counted;     /* items whose score was computed (rkm_topn)      */
+    int32_t retries;            /* capacity-overflow retries in the last call     */
+    int32_t exact_integer_path; /* 1 if the last call rescored with integers      */
+    double last_ms;             /* wall time of the last call, milliseconds       */
+    uint64_t kernel_launches;   /* kernels this library launched in the last call */
+    uint64_t threshold_launches;/* launches of the threshold product kernel       */
+    double phase_ms[RKM_PHASES];/* device time per phase (profile = 1), ms        */
+} rkm_stats;
+
+/* Fill `opts` with the defaults listed above. */
+RKM_API void rkm_default_opts(rkm_opts* opts);
+
+/* Create a context on CUDA device `device`.  `opts` may be NULL (defaults).
+ * Returns RKM_EINVAL for a bad option, RKM_ECUDA if the device is unusable. */
+RKM_API rkm_status rkm_create(rkm_ctx** out, const rkm_opts* opts, int device);
+
+/* Free the context and its device workspace.  NULL is accepted. */
+RKM_API void rkm_destroy(rkm_ctx* ctx);
+
+/* Message for the last error on this host thread ("" if none). */
+RKM_API const char* rkm_last_error(void);
+
+/* Library version string. */
+RKM_API const char* rkm_version(void);
+
+/*
+ * Thresholds -- Definition 1 for every user (the k-MIPS step of the first
+ * Section 2.2 baseline, which Algorithm 1 approximates with A_i^k).
+ *   U: device, n x d (stride ldu); P: device, m x d (stride ldp).
+ *   1 <= k <= min(m, k_max); n >= 0 (n == 0 is a no-op); 1 <= d <= 256;
+ *   n, m < 2^31.
+ *   tau:  device, [n] double  -- tau_u (a zero threshold is +0.0).
+ *   tid:  device, [n] int32   -- t_u, the k-th item of u.
+ *   topk: device, [n * k] int32 or NULL -- S_k(u) in order, row u at u*k.
+ */
+RKM_API rkm_status rkm_thresholds(rkm_ctx* ctx, const float* U, int64_t n, int64_t ldu,
+                          const float* P, int64_t m, int64_t ldp, int d, int k,
+                          double* tau, int32_t* tid, int32_t* topk, void* stream);
+
+/*
+ * Scores -- Eq. 1 / the second Section 2.2 baseline: score(p_i) = |T_k(p_i)|
+ * for every item, counted against given thresholds (tau, tid as produced by
+ * rkm_thresholds for the same U, P, k).
+ *   scores: device, [m] int32.
+ */
+RKM_API rkm_status rkm_scores(rkm_ctx* ctx, const float* U, int64_t n, int64_t ldu,
+                      const float* P, int64_t m, int64_t ldp, int d,
+                      const double* tau, const int32_t* tid, int32_t* scores,
+                      void* stream);
+
+/*
+ * Top-N -- Definition 3: thresholds, then item scores (skipping, when the
+ * filter option is on, every item whose Eq. 2 upper bound cannot reach the
+ * N-th score, in the spirit of Algorithm 2), then the N best items.
+ *   1 <= N <= min(m, 4096).  ids: device [N] int32; top_scores: device [N] int32, in
+ *   order (score descending, id ascending).
+ *   tau, tid: device [n] or NULL -- the thresholds computed on the way.
+ */
+RKM_API rkm_status rkm_topn(rkm_ctx* ctx, const float* U, int64_t n, int64_t ldu,
+                    const float* P, int64_t m, int64_t ldp, int d, int k, int N,
+                    int32_t* ids, int32_t* top_scores, double* tau, int32_t* tid,
+                    void* stream);
+
+/* rkm_topn with HOST buffers: copies U and P to the device (inside the call),
+ * runs rkm_topn and copies ids and top_scores back.  All pointers are host. */
+RKM_API rkm_status rkm_topn_host(rkm_ctx* ctx, const float* U, int64_t n, int64_t ldu,
+                         const float* P, int64_t m, int64_t ldp, int d, int k, int N,
+                         int32_t* ids, int32_t* top_scores, void* stream);
+
+/*
+ * Item upper bounds -- Eq. 2 with A_i^k = tau_u (Section 4.1):
+ * uscore[i] >= #{u : ||u|| ||p_i|| >= tau_u} >= score(p_i) (Theorem 2).
+ * The count is taken over users bucketed by tau_u / ||u|| (rounded outward),
+ * so it can exceed the exact count by the users of one bucket.
+ *   uscore: device [m] int32.
+ */
+RKM_API rkm_status rkm_item_bounds(rkm_ctx* ctx, const float* U, int64_t n, int64_t ldu,
+                           const float* P, int64_t m, int64_t ldp, int d,
+                           const double* tau, int32_t* uscore, void* stream);
+
+/*
+ * Serving -- keep users and their thresholds resident, then score new
+ * candidate items (Definition 2 for an item whose id exceeds every catalogue
+ * id, so a tie at tau_u does not make it a member; the catalogue and the
+ * thresholds are not updated).
+ * rkm_resident_set copies what it needs from U, tau, tid into the context.
+ */
+RKM_API rkm_status rkm_resident_set(rkm_ctx* ctx, const float* U, int64_t n, int64_t ldu, int d,
+                            const double* tau, const int32_t* tid, void* stream);
+
+/*   Q: device, q x d (stride ldq), q >= 0.  counts: device [q] int32,
+ *   counts[j] = #{u : u.Q_j > tau_u}.  Returns RKM_ESTATE without a resident set. */
+RKM_API rkm_status rkm_query_new_items(rkm_ctx* ctx, const float* Q, int64_t q, int64_t ldq,
+                               int32_t* counts, void* stream);
+
+/* Counters of the last call. */
+RKM_API rkm_status rkm_get_stats(const rkm_ctx* ctx, rkm_stats* out);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* RKM_H */

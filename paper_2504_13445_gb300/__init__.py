@@ -1,0 +1,266 @@
+"""GB300 reverse k-MIPS top-N (arXiv 2504.13445): thin Python binding of librkm.so.
+
+Every function here marshals arguments into the C ABI declared in include/rkm.h and
+calls it; all computation runs in the library's CUDA kernels.  PyTorch supplies
+device memory and the current CUDA stream only.  There is no fallback: if the
+library is missing the import of a binding function raises.
+
+Low-level names match the C ABI (``rkm_thresholds`` ...); ``Context`` wraps them.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "lib", "librkm.so")
+
+RKM_FP32, RKM_BF16, RKM_FP8 = 0, 1, 2
+PRECISIONS = {"fp32": RKM_FP32, "bf16": RKM_BF16, "fp8": RKM_FP8}
+STATUS = {0: "RKM_OK", 1: "RKM_EINVAL", 2: "RKM_ENOMEM", 3: "RKM_ECUDA", 4: "RKM_EOVERFLOW",
+          5: "RKM_ETIMEOUT", 6: "RKM_ESTATE", 7: "RKM_EINTERNAL"}
+
+EXPORTED = ["rkm_default_opts", "rkm_create", "rkm_destroy", "rkm_last_error", "rkm_version",
+            "rkm_thresholds", "rkm_scores", "rkm_topn", "rkm_topn_host", "rkm_item_bounds",
+            "rkm_resident_set", "rkm_query_new_items", "rkm_get_stats"]
+
+
+class RkmError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class Opts(ctypes.Structure):
+    _fields_ = [("precision", ctypes.c_int), ("k_max", ctypes.c_int), ("cand_capacity", ctypes.c_int),
+                ("band_capacity", ctypes.c_int64), ("filter", ctypes.c_int), ("profile", ctypes.c_int)]
+
+
+class Stats(ctypes.Structure):
+    _fields_ = [("pairs_total", ctypes.c_uint64), ("pairs_evaluated", ctypes.c_uint64),
+                ("candidates", ctypes.c_uint64), ("band_pairs", ctypes.c_uint64),
+                ("items_counted", ctypes.c_uint64), ("retries", ctypes.c_int32),
+                ("exact_integer_path", ctypes.c_int32), ("last_ms", ctypes.c_double),
+                ("kernel_launches", ctypes.c_uint64), ("threshold_launches", ctypes.c_uint64),
+                ("phase_ms", ctypes.c_double * 8)]
+
+    PHASES = ("prep", "threshold", "exact", "bounds", "count", "band", "topn", "unused")
+
+    def as_dict(self) -> dict:
+        out = {f: getattr(self, f) for f, _ in self._fields_ if f != "phase_ms"}
+        out["phase_ms"] = {name: self.phase_ms[i] for i, name in enumerate(self.PHASES[:7])}
+        return out
+
+
+_lib = None
+
+
+def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
+    """Load librkm.so (built by build.py); raises if it is missing."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError(f"librkm.so not found at {path}; run __graft_entry__.build() first")
+    lib = ctypes.CDLL(path)
+    P, I64, I, V = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int, None
+    sig = {
+        "rkm_default_opts": (V, [ctypes.POINTER(Opts)]),
+        "rkm_create": (I, [ctypes.POINTER(P), ctypes.POINTER(Opts), I]),
+        "rkm_destroy": (V, [P]),
+        "rkm_last_error": (ctypes.c_char_p, []),
+        "rkm_version": (ctypes.c_char_p, []),
+        "rkm_thresholds": (I, [P, P, I64, I64, P, I64, I64, I, I, P, P, P, P]),
+        "rkm_scores": (I, [P, P, I64, I64, P, I64, I64, I, P, P, P, P]),
+        "rkm_topn": (I, [P, P, I64, I64, P, I64, I64, I, I, I, P, P, P, P, P]),
+        "rkm_topn_host": (I, [P, P, I64, I64, P, I64, I64, I, I, I, P, P, P]),
+        "rkm_item_bounds": (I, [P, P, I64, I64, P, I64, I64, I, P, P, P]),
+        "rkm_resident_set": (I, [P, P, I64, I64, I, P, P, P]),
+        "rkm_query_new_items": (I, [P, P, I64, I64, P, P]),
+        "rkm_get_stats": (I, [P, ctypes.POINTER(Stats)]),
+    }
+    for name, (res, args) in sig.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+def _check(status: int) -> None:
+    if status != 0:
+        raise RkmError(status, load_library().rkm_last_error().decode())
+
+
+def _stream():
+    import torch
+    return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+def _ptr(t) -> ctypes.c_void_p:
+    return ctypes.c_void_p(t.data_ptr() if t is not None else 0)
+
+
+def _mat(X):
+    """A row-major float32 CUDA matrix with unit column stride: (tensor, rows, ld)."""
+    import torch
+    if not (isinstance(X, torch.Tensor) and X.is_cuda and X.dtype == torch.float32 and X.dim() == 2):
+        raise TypeError("expected a 2-D float32 CUDA tensor")
+    if X.stride(1) != 1:
+        X = X.contiguous()
+    return X, X.shape[0], X.stride(0) if X.shape[0] > 0 else X.shape[1]
+
+
+# ---------------------------------------------------------------- C-ABI names
+
+def rkm_create(precision: str = "bf16", device: int = 0, k_max: int = 64, cand_capacity: int = 0,
+               band_capacity: int = 0, filter: bool = True, profile: bool = False) -> ctypes.c_void_p:
+    lib = load_library()
+    o = Opts()
+    lib.rkm_default_opts(ctypes.byref(o))
+    o.precision = PRECISIONS[precision]
+    o.k_max = k_max
+    o.cand_capacity = cand_capacity
+    o.band_capacity = band_capacity
+    o.filter = 1 if filter else 0
+    o.profile = 1 if profile else 0
+    h = ctypes.c_void_p()
+    _check(lib.rkm_create(ctypes.byref(h), ctypes.byref(o), device))
+    return h
+
+
+def rkm_destroy(ctx) -> None:
+    load_library().rkm_destroy(ctx)
+
+
+def rkm_thresholds(ctx, U, P, k: int, want_topk: bool = False):
+    import torch
+    U, n, ldu = _mat(U)
+    P, m, ldp = _mat(P)
+    d = U.shape[1]
+    tau = torch.empty(n, dtype=torch.float64, device=U.device)
+    tid = torch.empty(n, dtype=torch.int32, device=U.device)
+    topk = torch.empty((n, k), dtype=torch.int32, device=U.device) if want_topk else None
+    _check(load_library().rkm_thresholds(ctx, _ptr(U), n, ldu, _ptr(P), m, ldp, d, k, _ptr(tau), _ptr(tid),
+                                         _ptr(topk), _stream()))
+    return tau, tid, topk
+
+
+def rkm_scores(ctx, U, P, tau, tid):
+    import torch
+    U, n, ldu = _mat(U)
+    P, m, ldp = _mat(P)
+    scores = torch.empty(m, dtype=torch.int32, device=U.device)
+    _check(load_library().rkm_scores(ctx, _ptr(U), n, ldu, _ptr(P), m, ldp, U.shape[1],
+                                     _ptr(tau.contiguous()), _ptr(tid.contiguous()), _ptr(scores), _stream()))
+    return scores
+
+
+def rkm_topn(ctx, U, P, k: int, N: int, return_thresholds: bool = False):
+    import torch
+    U, n, ldu = _mat(U)
+    P, m, ldp = _mat(P)
+    ids = torch.empty(N, dtype=torch.int32, device=U.device)
+    sc = torch.empty(N, dtype=torch.int32, device=U.device)
+    tau = torch.empty(n, dtype=torch.float64, device=U.device) if return_thresholds else None
+    tid = torch.empty(n, dtype=torch.int32, device=U.device) if return_thresholds else None
+    _check(load_library().rkm_topn(ctx, _ptr(U), n, ldu, _ptr(P), m, ldp, U.shape[1], k, N, _ptr(ids), _ptr(sc),
+                                   _ptr(tau), _ptr(tid), _stream()))
+    return (ids, sc, tau, tid) if return_thresholds else (ids, sc)
+
+
+def rkm_topn_host(ctx, U, P, k: int, N: int):
+    """Host numpy float32 inputs and outputs; the copies happen inside the library call."""
+    import numpy as np
+    U = np.ascontiguousarray(U, dtype=np.float32)
+    P = np.ascontiguousarray(P, dtype=np.float32)
+    ids = np.empty(N, dtype=np.int32)
+    sc = np.empty(N, dtype=np.int32)
+    _check(load_library().rkm_topn_host(ctx, U.ctypes.data_as(ctypes.c_void_p), U.shape[0], U.shape[1],
+                                        P.ctypes.data_as(ctypes.c_void_p), P.shape[0], P.shape[1], U.shape[1],
+                                        k, N, ids.ctypes.data_as(ctypes.c_void_p),
+                                        sc.ctypes.data_as(ctypes.c_void_p), _stream()))
+    return ids, sc
+
+
+def rkm_item_bounds(ctx, U, P, tau):
+    import torch
+    U, n, ldu = _mat(U)
+    P, m, ldp = _mat(P)
+    us = torch.empty(m, dtype=torch.int32, device=U.device)
+    _check(load_library().rkm_item_bounds(ctx, _ptr(U), n, ldu, _ptr(P), m, ldp, U.shape[1],
+                                          _ptr(tau.contiguous()), _ptr(us), _stream()))
+    return us
+
+
+def rkm_resident_set(ctx, U, tau, tid) -> None:
+    U, n, ldu = _mat(U)
+    _check(load_library().rkm_resident_set(ctx, _ptr(U), n, ldu, U.shape[1], _ptr(tau.contiguous()),
+                                           _ptr(tid.contiguous()), _stream()))
+
+
+def rkm_query_new_items(ctx, Q):
+    import torch
+    Q, q, ldq = _mat(Q)
+    counts = torch.empty(q, dtype=torch.int32, device=Q.device)
+    _check(load_library().rkm_query_new_items(ctx, _ptr(Q), q, ldq, _ptr(counts), _stream()))
+    return counts
+
+
+def rkm_get_stats(ctx) -> dict:
+    s = Stats()
+    _check(load_library().rkm_get_stats(ctx, ctypes.byref(s)))
+    return s.as_dict()
+
+
+def rkm_version() -> str:
+    return load_library().rkm_version().decode()
+
+
+class Context:
+    """Owns one rkm_ctx (device workspace, resident serving state)."""
+
+    def __init__(self, precision: str = "bf16", device: int = 0, **opts):
+        self.precision = precision
+        self.handle = rkm_create(precision, device, **opts)
+
+    def close(self) -> None:
+        if self.handle:
+            rkm_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def thresholds(self, U, P, k, want_topk=False):
+        return rkm_thresholds(self.handle, U, P, k, want_topk)
+
+    def scores(self, U, P, tau, tid):
+        return rkm_scores(self.handle, U, P, tau, tid)
+
+    def topn(self, U, P, k, N, return_thresholds=False):
+        return rkm_topn(self.handle, U, P, k, N, return_thresholds)
+
+    def topn_host(self, U, P, k, N):
+        return rkm_topn_host(self.handle, U, P, k, N)
+
+    def item_bounds(self, U, P, tau):
+        return rkm_item_bounds(self.handle, U, P, tau)
+
+    def resident_set(self, U, tau, tid):
+        rkm_resident_set(self.handle, U, tau, tid)
+
+    def query_new_items(self, Q):
+        return rkm_query_new_items(self.handle, Q)
+
+    def stats(self) -> dict:
+        return rkm_get_stats(self.handle)

@@ -1,0 +1,83 @@
+// Shared definitions for the reverse k-MIPS kernels (device side).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+#include <stdint.h>
+#include <string.h>
+
+namespace rkm {
+
+// Tile shapes.  BU users (TMEM lanes / SIMT rows) by BI items per product tile.
+constexpr int BU = 128;
+constexpr int BI_SIMT = 128;
+constexpr int BI_TC = 256;
+constexpr int KMAX = 64;          // largest k the on-chip heaps hold
+constexpr int NMAX_TOPN = 4096;   // largest N the single-CTA top-N select holds
+constexpr int NBUCKET = 65536;    // buckets of the 16-bit float keys
+
+// Device-side status and counters of one call.  Zeroed before each call.
+struct DevStatus {
+    unsigned int cand_overflow;   // a user's candidate list stayed full after compaction
+    unsigned int band_overflow;   // the band queue was full
+    unsigned int internal_error;  // a consistency check failed (e.g. < k candidates)
+    unsigned int timeout;         // a bounded wait gave up
+    unsigned int grid_u;          // 1 while every user row is on the 2^-12 grid
+    unsigned int grid_p;          // 1 while every item row is on the grid
+    unsigned int band_count;      // pairs pushed to the band queue (may exceed capacity)
+    unsigned int band_done;       // pairs of the queue already rescored
+    unsigned int ticket;          // work ticket of the persistent counting kernel
+    unsigned int units_total;     // work units of the current counting stage
+    int t_end;                    // one past the last item tile of the filtered stage
+    int m_counted;                // items whose scores are complete (rkm_topn)
+    unsigned long long cand_total;      // candidates kept for exact rescoring
+    unsigned long long pairs_evaluated; // products computed by the counting pass
+    unsigned long long pad[4];
+};
+
+// Candidate of the threshold pass: an upper bound of u.p and the item's sorted position.
+struct Cand {
+    float ub;
+    int pos;
+};
+
+// Monotone map float -> uint32 (total order of non-NaN floats, -0 < +0).
+__host__ __device__ __forceinline__ uint32_t float_key(float x) {
+    uint32_t b;
+#ifdef __CUDA_ARCH__
+    b = __float_as_uint(x);
+#else
+    memcpy(&b, &x, 4);
+#endif
+    return (b & 0x80000000u) ? ~b : (b | 0x80000000u);
+}
+
+// 16-bit bucket of a float, monotone non-decreasing in x.
+__host__ __device__ __forceinline__ uint32_t bucket16(float x) { return float_key(x) >> 16; }
+
+// Monotone map double -> uint64 for the exact scores; callers add +0.0 first so
+// that -0.0 and +0.0 share one key.
+__device__ __forceinline__ unsigned long long double_key(double s) {
+    unsigned long long b = (unsigned long long)__double_as_longlong(s);
+    return (b & 0x8000000000000000ull) ? ~b : (b | 0x8000000000000000ull);
+}
+
+__device__ __forceinline__ float warp_max(float v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
+    return v;
+}
+
+template <typename T>
+__device__ __forceinline__ T warp_sum(T v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// Error bound of one approximate product, E = coef * ||u|| * ||p||max + eabs, rounded up.
+__device__ __forceinline__ float err_bound(float coef, float eabs, float un, float pn) {
+    return __fadd_ru(__fmul_ru(coef, __fmul_ru(un, pn)), eabs);
+}
+
+}  // namespace rkm

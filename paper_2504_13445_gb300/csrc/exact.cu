@@ -1,0 +1,182 @@
+// Exact rescoring: K3 (exact tau_u, t_u and S_k(u) from the candidate lists, Definition 1),
+// K6 (exact membership of the counting pass's band pairs, Eq. 1) and K8 (scores as the
+// histogram of S_k(u), the first Section 2.2 baseline).
+//
+// Exact inner products.  When every row is on the grid 2^e * q / 4096, u.p equals
+// 2^(e_u + e_p - 24) * sum_j q_u[j] q_p[j]; the integer sum is formed in 32-bit chunks of
+// 64 terms (each |term| <= 2^24, so a chunk stays below 2^30) added in 64 bits, then
+// scaled exactly into FP64.  Otherwise u.p is the left-to-right FP64 sum of the exact
+// FP64 products of the FP32 inputs.
+#include <cuda_runtime.h>
+
+#include "common.cuh"
+#include "kernels.h"
+
+namespace rkm {
+
+namespace {
+
+__device__ __forceinline__ double exact_dot(const ExactData& x, bool grid, int64_t u, int64_t i) {
+    double s;
+    if (grid) {
+        const int4* a = reinterpret_cast<const int4*>(x.qu + u * x.dq);
+        const int4* b = reinterpret_cast<const int4*>(x.qp + i * x.dq);
+        long long acc = 0;
+        const int vecs = x.dq >> 3;  // 8 int16 per int4
+        for (int v0 = 0; v0 < vecs; v0 += 8) {
+            int part = 0;
+            const int v1 = (v0 + 8 < vecs) ? v0 + 8 : vecs;  // 8 vectors = 64 terms
+            for (int v = v0; v < v1; ++v) {
+                const int4 av = a[v], bv = b[v];
+                const int aw[4] = {av.x, av.y, av.z, av.w};
+                const int bw[4] = {bv.x, bv.y, bv.z, bv.w};
+#pragma unroll
+                for (int h = 0; h < 4; ++h) {
+                    const int alo = (int)(int16_t)(aw[h] & 0xffff), ahi = aw[h] >> 16;
+                    const int blo = (int)(int16_t)(bw[h] & 0xffff), bhi = bw[h] >> 16;
+                    part += alo * blo + ahi * bhi;
+                }
+            }
+            acc += part;
+        }
+        s = ldexp((double)acc, x.eu[u] + x.ep[i] - 24);
+    } else {
+        const float* a = x.U + u * x.ldu;
+        const float* b = x.P + i * x.ldp;
+        s = 0.0;
+        for (int j = 0; j < x.d; ++j) s = fma((double)a[j], (double)b[j], s);
+    }
+    return s + 0.0;  // -0.0 -> +0.0
+}
+
+__device__ __forceinline__ double key_to_double(unsigned long long k) {
+    unsigned long long b = (k & 0x8000000000000000ull) ? (k ^ 0x8000000000000000ull) : ~k;
+    return __longlong_as_double((long long)b);
+}
+
+// One warp per user.
+__global__ void k_exact_tau(ExactData x, const Cand* __restrict__ cand, const int* __restrict__ cand_cnt,
+                            const float* __restrict__ lfin, int cap, const int* __restrict__ item_perm,
+                            int64_t n, int k, unsigned long long* __restrict__ keys,
+                            int* __restrict__ kid, double* __restrict__ tau, int* __restrict__ tid,
+                            int* __restrict__ topk, DevStatus* st) {
+    const int lane = threadIdx.x & 31;
+    const unsigned lt_mask = (1u << lane) - 1u;
+    const bool grid = *x.grid != 0u;
+    const int64_t warps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    unsigned long long kept_total = 0;
+    for (int64_t u = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; u < n; u += warps) {
+        const float L = lfin[u];
+        const int cnt = cand_cnt[u];
+        const Cand* c = cand + u * (int64_t)cap;
+        unsigned long long* kk = keys + u * (int64_t)cap;
+        int* ki = kid + u * (int64_t)cap;
+        int kept = 0;
+        for (int base = 0; base < cnt; base += 32) {
+            const int j = base + lane;
+            bool keep = false;
+            Cand cj;
+            cj.ub = 0.f;
+            cj.pos = 0;
+            if (j < cnt) {
+                cj = c[j];
+                keep = cj.ub >= L;
+            }
+            const unsigned mask = __ballot_sync(0xffffffffu, keep);
+            if (keep) {
+                const int slot = kept + __popc(mask & lt_mask);
+                const int io = item_perm[cj.pos];
+                kk[slot] = double_key(exact_dot(x, grid, u, io));
+                ki[slot] = io;
+            }
+            kept += __popc(mask);
+        }
+        __syncwarp();
+        if (lane == 0) kept_total += (unsigned long long)kept;
+        if (kept < k) {
+            if (lane == 0) st->internal_error = 1u;
+            continue;
+        }
+        for (int j = lane; j < kept; j += 32) {
+            const unsigned long long key = kk[j];
+            const int id = ki[j];
+            int rank = 0;
+            for (int r = 0; r < kept; ++r) {
+                const unsigned long long k2 = kk[r];
+                rank += (k2 > key) || (k2 == key && ki[r] < id);
+            }
+            if (rank < k) {
+                if (topk) topk[u * (int64_t)k + rank] = id;
+                if (rank == k - 1) {
+                    tau[u] = key_to_double(key);
+                    tid[u] = id;
+                }
+            }
+        }
+        __syncwarp();
+    }
+    kept_total = warp_sum(kept_total);
+    if (lane == 0 && kept_total) atomicAdd(&st->cand_total, kept_total);
+}
+
+__global__ void k_band_rescore(ExactData x, const int2* __restrict__ band, unsigned band_cap,
+                               const int* __restrict__ item_perm, const double* __restrict__ tau,
+                               const int* __restrict__ tid, bool new_items, int* __restrict__ counts,
+                               DevStatus* st) {
+    const bool grid = *x.grid != 0u;
+    const unsigned begin = st->band_done;
+    unsigned end = st->band_count;
+    if (end > band_cap) end = band_cap;
+    for (unsigned e = begin + blockIdx.x * blockDim.x + threadIdx.x; e < end; e += gridDim.x * blockDim.x) {
+        const int2 b = band[e];
+        const int64_t u = b.x;
+        const int io = item_perm[b.y];
+        const double s = exact_dot(x, grid, u, io);
+        const double t = tau[u];
+        const bool member = (s > t) || (!new_items && s == t && io <= tid[u]);
+        if (member) atomicAdd(&counts[b.y], 1);
+    }
+}
+
+__global__ void k_band_mark(DevStatus* st, unsigned band_cap) {
+    unsigned end = st->band_count;
+    st->band_done = end > band_cap ? band_cap : end;
+}
+
+__global__ void k_histogram(const int* __restrict__ topk, int64_t nk, int* __restrict__ scores) {
+    for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < nk; j += (int64_t)gridDim.x * blockDim.x)
+        atomicAdd(&scores[topk[j]], 1);
+}
+
+}  // namespace
+
+void launch_exact_tau(const ExactData& x, const Cand* cand, const int* cand_cnt, const float* lfin, int cap,
+                      const int* item_perm, int64_t n, int k, unsigned long long* keys, int* kid,
+                      double* tau, int* tid, int* topk, DevStatus* st, cudaStream_t s) {
+    if (n <= 0) return;
+    int64_t blocks = (n * 32 + 255) / 256;
+    if (blocks > 65536) blocks = 65536;
+    note_launch();
+    k_exact_tau<<<(int)blocks, 256, 0, s>>>(x, cand, cand_cnt, lfin, cap, item_perm, n, k, keys, kid, tau,
+                                            tid, topk, st);
+}
+
+void launch_band_rescore(const ExactData& x, const int2* band, unsigned band_cap, const int* item_perm,
+                         int64_t m_ids, const double* tau, const int* tid, bool new_items, int* counts,
+                         DevStatus* st, cudaStream_t s) {
+    (void)m_ids;
+    note_launch();
+    k_band_rescore<<<1184, 256, 0, s>>>(x, band, band_cap, item_perm, tau, tid, new_items, counts, st);
+    note_launch();
+    k_band_mark<<<1, 1, 0, s>>>(st, band_cap);
+}
+
+void launch_histogram(const int* topk, int64_t nk, int* scores, cudaStream_t s) {
+    if (nk <= 0) return;
+    int64_t blocks = (nk + 255) / 256;
+    if (blocks > 65536) blocks = 65536;
+    note_launch();
+    k_histogram<<<(int)blocks, 256, 0, s>>>(topk, nk, scores);
+}
+
+}  // namespace rkm

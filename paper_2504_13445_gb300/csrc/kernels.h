@@ -1,0 +1,143 @@
+// Internal launchers of the reverse k-MIPS kernels (host side, not part of the C ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <atomic>
+
+#include "common.cuh"
+
+namespace rkm {
+
+// Kernels launched by this library since load (each launcher calls note_launch()).
+extern std::atomic<unsigned long long> g_launches;
+inline void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+
+// ---- prep.cu (K1 prep, K4 bounds and the bucket sort) ------------------------------
+
+// Per row: exponent e (max|x| <= 2^e), integer grid codes q = x * 2^(12-e) (int16,
+// row stride dq), exact/upper-bound squared norm, ||x|| rounded up, grid flag.
+void launch_prep_rows(const float* X, int64_t rows, int64_t ld, int d, int* ex, int16_t* q,
+                      int dq, double* norm2, float* nrm_hi, unsigned* grid_flag, cudaStream_t s);
+
+// Zero-padded operand copy dst[r][c] (rows_pad x dp) of X (row perm[r] if perm != null).
+void launch_pack_f32(const float* X, int64_t rows, int64_t ld, int d, const int* perm,
+                     float* dst, int64_t rows_pad, int dp, cudaStream_t s);
+void launch_pack_bf16(const float* X, int64_t rows, int64_t ld, int d, const int* perm,
+                      __nv_bfloat16* dst, int64_t rows_pad, int dp, cudaStream_t s);
+
+// Counting sort of `count` float keys by their 16-bit bucket (ascending, or descending
+// when `descending`).  Writes perm[pos] = source index and, if cum != null, the
+// inclusive prefix count of each bucket (in sort order).  hist: NBUCKET uints scratch.
+void launch_bucket_sort(const float* keys, int64_t count, bool descending, unsigned* hist,
+                        unsigned* offs, int* perm, unsigned* cum, cudaStream_t s);
+
+// gathered[i] = src[perm[i]] for float / double / int arrays.
+void launch_gather_f32(const float* src, const int* perm, int64_t count, float* dst, cudaStream_t s);
+void launch_gather_f64(const double* src, const int* perm, int64_t count, double* dst, cudaStream_t s);
+void launch_gather_i32(const int* src, const int* perm, int64_t count, int* dst, cudaStream_t s);
+
+// Maximum of vals[t*tile .. min(count,(t+1)*tile)) per tile (0 for an empty tile).
+void launch_tile_max(const float* vals, int64_t count, int tile, int64_t tiles, float* out,
+                     cudaStream_t s);
+
+// K4: r_u = tau_u / ||u|| rounded down (-inf when tau_u <= 0).
+void launch_user_ratio(const double* tau, const double* norm2, int64_t n, float* r, cudaStream_t s);
+
+// K4: uscore[i] = number of users whose ratio bucket <= bucket(||p_i||) (ucum lookup).
+void launch_item_uscore(const float* nrm_hi, int64_t m, const unsigned* ucum, int* uscore,
+                        cudaStream_t s);
+
+// ---- threshold pass (K2) ------------------------------------------------------------
+
+struct ThresholdArgs {
+    const void* A;        // users, packed [n_pad][dp] (fp32 or bf16), original order
+    const void* B;        // items, packed [m_pad][dp], sorted by norm (descending)
+    int64_t n, m;
+    int dp, k, cap;
+    const float* unrm;    // [n] ||u|| rounded up
+    const float* tmax;    // [item tiles] max ||p|| of the tile, rounded up
+    float coef, eabs;     // error bound E = coef*||u||*tmax + eabs
+    Cand* cand;           // [n][cap]
+    int* cand_cnt;        // [n]
+    float* lfin;          // [n] final lower threshold L_u
+    DevStatus* st;
+    int num_sms;
+};
+void launch_threshold_simt(const ThresholdArgs& a, cudaStream_t s);
+void launch_threshold_tc(const ThresholdArgs& a, const void* tmapA, const void* tmapB,
+                         cudaStream_t s);
+
+// ---- exact rescoring (K3, K6, K8) ---------------------------------------------------
+
+struct ExactData {
+    // user side (original order)
+    const float* U; int64_t ldu;
+    const int* eu; const int16_t* qu;
+    // item side (original order)
+    const float* P; int64_t ldp;
+    const int* ep; const int16_t* qp;
+    int d, dq;
+    const unsigned* grid;  // device flag: nonzero = use the integer path
+};
+
+// K3: exact tau_u, t_u and (optionally) S_k(u) from the candidate lists.
+void launch_exact_tau(const ExactData& x, const Cand* cand, const int* cand_cnt, const float* lfin,
+                      int cap, const int* item_perm, int64_t n, int k,
+                      unsigned long long* keys, int* kid, double* tau, int* tid, int* topk,
+                      DevStatus* st, cudaStream_t s);
+
+// K6: rescore queued band pairs (orig user, sorted item pos) and add members to counts.
+void launch_band_rescore(const ExactData& x, const int2* band, unsigned band_cap,
+                         const int* item_perm, int64_t m_ids, const double* tau, const int* tid,
+                         bool new_items, int* counts, DevStatus* st, cudaStream_t s);
+
+// K8: scores by histogram of S_k(u) (the first Section 2.2 baseline).
+void launch_histogram(const int* topk, int64_t nk, int* scores, cudaStream_t s);
+
+// ---- counting pass (K5) -------------------------------------------------------------
+
+struct CountArgs {
+    const void* A;          // users packed in ratio order [n_pad][dp]
+    const void* B;          // items packed sorted [m_pad][dp]
+    int64_t n, m;
+    int dp;
+    const float* unrm_s;    // [n] ||u|| rounded up, ratio order
+    const double* tau_s;    // [n] ratio order
+    const int* tid_s;       // [n] ratio order (ignored for new items)
+    const int* uperm;       // ratio order -> original user id
+    const int* item_id;     // sorted pos -> original item id (null for new items)
+    bool new_items;         // strict rule u.p > tau_u (new ids beat no tie)
+    const float* tmax;      // per item tile
+    const int* nprefix;     // per item tile: users needed (ratio-order prefix length)
+    const unsigned* unit_off;  // [tiles+1] work units per item tile, exclusive scan
+    int t_begin;            // first item tile of the stage
+    int group;              // user tiles per work unit
+    float coef, eabs;
+    int* counts;            // [m] by sorted position
+    int2* band; unsigned band_cap;
+    DevStatus* st;
+    int num_sms;
+};
+// Work list of a counting stage over item tiles [t_begin, t_end or *t_end_dev).
+void launch_build_units(const float* tmax, const unsigned* ucum, int t_begin, int t_end,
+                        const int* t_end_dev, int tile_users, int group, int* nprefix,
+                        unsigned* unit_off, DevStatus* st, cudaStream_t s);
+void launch_count_simt(const CountArgs& a, cudaStream_t s);
+void launch_count_tc(const CountArgs& a, const void* tmapA, const void* tmapB, cudaStream_t s);
+
+// ---- top-N (K7) ---------------------------------------------------------------------
+
+// Top N of key = (count << 32) | (0xFFFFFFFF - id) over positions [0, m_lim) where
+// m_lim = *m_lim_dev if non-null else m.  ids/scores in order.
+void launch_topn(const int* counts, const int* item_id, int64_t m, const int* m_lim_dev, int N,
+                 int* ids, int* scores, DevStatus* st, cudaStream_t s);
+
+// Filter cut: with LB = N-th score among the first c0 positions (from ids/scores of a
+// top-N over them), set st->t_end to the first item tile whose uscore bound is < LB.
+void launch_filter_cut(const int* top_scores_c0, int N, const float* tmax, const unsigned* ucum,
+                       int64_t tiles, int t_begin, int tile_items, int64_t m, DevStatus* st,
+                       cudaStream_t s);
+
+}  // namespace rkm

@@ -1,0 +1,277 @@
+// K1 (prep) and K4 (Eq. 2 bounds) kernels, plus the 16-bit bucket counting sort.
+//
+// Prep follows step (1) of Algorithm 1 (norms of every vector, items ordered by
+// descending norm) and adds what the GPU path needs: the exact grid codes for
+// exact rescoring and zero-padded operand copies for the product kernels.
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+#include <math.h>
+
+#include "common.cuh"
+#include "kernels.h"
+
+namespace rkm {
+
+namespace {
+
+inline int grid_for(int64_t work, int per_block, int cap = 1 << 20) {
+    int64_t g = (work + per_block - 1) / per_block;
+    if (g < 1) g = 1;
+    if (g > cap) g = cap;
+    return (int)g;
+}
+
+// One warp per row.  The row is on the grid iff every x * 2^(12-e) is an integer of
+// magnitude <= 4096; then ||x||^2 = sum(q^2) * 2^(2e-24) exactly.
+__global__ void k_prep_rows(const float* __restrict__ X, int64_t rows, int64_t ld, int d,
+                            int* __restrict__ ex, int16_t* __restrict__ q, int dq,
+                            double* __restrict__ norm2, float* __restrict__ nrm_hi,
+                            unsigned* grid_flag) {
+    const int lane = threadIdx.x & 31;
+    const int64_t warps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t row = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; row < rows; row += warps) {
+        const float* x = X + row * ld;
+        float mx = 0.f;
+        for (int j = lane; j < d; j += 32) mx = fmaxf(mx, fabsf(x[j]));
+        mx = warp_max(mx);
+        int e = 0;
+        if (mx > 0.f) {
+            int E;
+            float f = frexpf(mx, &E);
+            e = (f == 0.5f) ? E - 1 : E;
+        }
+        bool ok = true;
+        long long s2 = 0;
+        double d2 = 0.0;
+        for (int j = lane; j < dq; j += 32) {
+            float v = (j < d) ? x[j] : 0.f;
+            float t = ldexpf(v, 12 - e);
+            bool gi = (t == rintf(t)) && fabsf(t) <= 4096.f;
+            ok = ok && gi;
+            int qi = gi ? (int)t : 0;
+            q[row * dq + j] = (int16_t)qi;
+            s2 += (long long)qi * qi;
+            d2 = fma((double)v, (double)v, d2);
+        }
+        ok = __all_sync(0xffffffffu, ok);
+        s2 = warp_sum(s2);
+        d2 = warp_sum(d2);
+        if (lane == 0) {
+            double n2;
+            if (ok) {
+                n2 = ldexp((double)s2, 2 * e - 24);
+            } else {
+                // FP64 sum of exact squares: relative error below d * 2^-53; widen by 2^-40.
+                n2 = d2 * (1.0 + 0x1p-40);
+                atomicAnd(grid_flag, 0u);
+            }
+            ex[row] = e;
+            norm2[row] = n2;
+            nrm_hi[row] = __double2float_ru(__dsqrt_ru(n2));
+        }
+    }
+}
+
+template <typename T>
+__device__ __forceinline__ T cvt_from_float(float v);
+template <>
+__device__ __forceinline__ float cvt_from_float<float>(float v) { return v; }
+template <>
+__device__ __forceinline__ __nv_bfloat16 cvt_from_float<__nv_bfloat16>(float v) {
+    return __float2bfloat16_rn(v);
+}
+
+template <typename T>
+__global__ void k_pack(const float* __restrict__ X, int64_t rows, int64_t ld, int d,
+                       const int* __restrict__ perm, T* __restrict__ dst, int64_t rows_pad, int dp) {
+    const int64_t total = rows_pad * dp;
+    for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
+         idx += (int64_t)gridDim.x * blockDim.x) {
+        int64_t r = idx / dp;
+        int c = (int)(idx - r * dp);
+        float v = 0.f;
+        if (r < rows && c < d) {
+            int64_t src = perm ? (int64_t)perm[r] : r;
+            v = X[src * ld + c];
+        }
+        dst[idx] = cvt_from_float<T>(v);
+    }
+}
+
+__global__ void k_hist(const float* __restrict__ keys, int64_t count, bool desc,
+                       unsigned* __restrict__ hist) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < count;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        unsigned b = bucket16(keys[i]);
+        if (desc) b = (NBUCKET - 1) - b;
+        atomicAdd(&hist[b], 1u);
+    }
+}
+
+// Single block: exclusive scan of hist into offs, inclusive into cum (if non-null).
+__global__ void k_scan_hist(const unsigned* __restrict__ hist, unsigned* __restrict__ offs,
+                            unsigned* __restrict__ cum) {
+    constexpr int T = 1024;
+    constexpr int PER = NBUCKET / T;  // 64 consecutive buckets per thread
+    __shared__ unsigned part[T];
+    const int t = threadIdx.x;
+    unsigned local = 0;
+    for (int j = 0; j < PER; ++j) local += hist[t * PER + j];
+    part[t] = local;
+    __syncthreads();
+    // Hillis-Steele inclusive scan over the 1024 partial sums.
+    for (int o = 1; o < T; o <<= 1) {
+        unsigned v = (t >= o) ? part[t - o] : 0u;
+        __syncthreads();
+        part[t] += v;
+        __syncthreads();
+    }
+    unsigned run = part[t] - local;
+    for (int j = 0; j < PER; ++j) {
+        unsigned h = hist[t * PER + j];
+        offs[t * PER + j] = run;
+        run += h;
+        if (cum) cum[t * PER + j] = run;
+    }
+}
+
+__global__ void k_scatter(const float* __restrict__ keys, int64_t count, bool desc,
+                          unsigned* __restrict__ offs, int* __restrict__ perm) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < count;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        unsigned b = bucket16(keys[i]);
+        if (desc) b = (NBUCKET - 1) - b;
+        unsigned pos = atomicAdd(&offs[b], 1u);
+        perm[pos] = (int)i;
+    }
+}
+
+template <typename T>
+__global__ void k_gather(const T* __restrict__ src, const int* __restrict__ perm, int64_t count,
+                         T* __restrict__ dst) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < count;
+         i += (int64_t)gridDim.x * blockDim.x)
+        dst[i] = src[perm[i]];
+}
+
+__global__ void k_tile_max(const float* __restrict__ vals, int64_t count, int tile, int64_t tiles,
+                           float* __restrict__ out) {
+    const int lane = threadIdx.x & 31;
+    const int64_t warps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t t = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; t < tiles; t += warps) {
+        float mx = 0.f;
+        int64_t b = t * tile, e = b + tile;
+        if (e > count) e = count;
+        for (int64_t i = b + lane; i < e; i += 32) mx = fmaxf(mx, vals[i]);
+        mx = warp_max(mx);
+        if (lane == 0) out[t] = mx;
+    }
+}
+
+// r_u <= tau_u / ||u||: divide by an upper bound of ||u|| rounding down, then round the
+// FP64 quotient down to FP32.  Users with tau_u <= 0 keep every item (r = -inf).
+__global__ void k_user_ratio(const double* __restrict__ tau, const double* __restrict__ norm2,
+                             int64_t n, float* __restrict__ r) {
+    for (int64_t u = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; u < n;
+         u += (int64_t)gridDim.x * blockDim.x) {
+        double t = tau[u];
+        float v = -INFINITY;
+        if (t > 0.0) {
+            double nu = __dsqrt_ru(norm2[u]);
+            v = __double2float_rd(__ddiv_rd(t, nu));
+        }
+        r[u] = v;
+    }
+}
+
+__global__ void k_item_uscore(const float* __restrict__ nrm_hi, int64_t m,
+                              const unsigned* __restrict__ ucum, int* __restrict__ uscore) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m;
+         i += (int64_t)gridDim.x * blockDim.x)
+        uscore[i] = (int)ucum[bucket16(nrm_hi[i])];
+}
+
+}  // namespace
+
+void launch_prep_rows(const float* X, int64_t rows, int64_t ld, int d, int* ex, int16_t* q, int dq,
+                      double* norm2, float* nrm_hi, unsigned* grid_flag, cudaStream_t s) {
+    if (rows <= 0) return;
+    note_launch();
+    k_prep_rows<<<grid_for(rows * 32, 256, 65536), 256, 0, s>>>(X, rows, ld, d, ex, q, dq, norm2,
+                                                                 nrm_hi, grid_flag);
+}
+
+void launch_pack_f32(const float* X, int64_t rows, int64_t ld, int d, const int* perm, float* dst,
+                     int64_t rows_pad, int dp, cudaStream_t s) {
+    if (rows_pad <= 0) return;
+    note_launch();
+    k_pack<float><<<grid_for(rows_pad * dp, 256, 65536), 256, 0, s>>>(X, rows, ld, d, perm, dst,
+                                                                      rows_pad, dp);
+}
+
+void launch_pack_bf16(const float* X, int64_t rows, int64_t ld, int d, const int* perm,
+                      __nv_bfloat16* dst, int64_t rows_pad, int dp, cudaStream_t s) {
+    if (rows_pad <= 0) return;
+    note_launch();
+    k_pack<__nv_bfloat16><<<grid_for(rows_pad * dp, 256, 65536), 256, 0, s>>>(X, rows, ld, d, perm,
+                                                                              dst, rows_pad, dp);
+}
+
+void launch_bucket_sort(const float* keys, int64_t count, bool descending, unsigned* hist,
+                        unsigned* offs, int* perm, unsigned* cum, cudaStream_t s) {
+    cudaMemsetAsync(hist, 0, NBUCKET * sizeof(unsigned), s);
+    if (count > 0) {
+        note_launch();
+        k_hist<<<grid_for(count, 256, 4096), 256, 0, s>>>(keys, count, descending, hist);
+    }
+    note_launch();
+    k_scan_hist<<<1, 1024, 0, s>>>(hist, offs, cum);
+    if (count > 0) {
+        note_launch();
+        k_scatter<<<grid_for(count, 256, 4096), 256, 0, s>>>(keys, count, descending, offs, perm);
+    }
+}
+
+void launch_gather_f32(const float* src, const int* perm, int64_t count, float* dst, cudaStream_t s) {
+    if (count > 0) {
+        note_launch();
+        k_gather<float><<<grid_for(count, 256, 65536), 256, 0, s>>>(src, perm, count, dst);
+    }
+}
+void launch_gather_f64(const double* src, const int* perm, int64_t count, double* dst, cudaStream_t s) {
+    if (count > 0) {
+        note_launch();
+        k_gather<double><<<grid_for(count, 256, 65536), 256, 0, s>>>(src, perm, count, dst);
+    }
+}
+void launch_gather_i32(const int* src, const int* perm, int64_t count, int* dst, cudaStream_t s) {
+    if (count > 0) {
+        note_launch();
+        k_gather<int><<<grid_for(count, 256, 65536), 256, 0, s>>>(src, perm, count, dst);
+    }
+}
+
+void launch_tile_max(const float* vals, int64_t count, int tile, int64_t tiles, float* out,
+                     cudaStream_t s) {
+    if (tiles > 0) {
+        note_launch();
+        k_tile_max<<<grid_for(tiles * 32, 256, 65536), 256, 0, s>>>(vals, count, tile, tiles, out);
+    }
+}
+
+void launch_user_ratio(const double* tau, const double* norm2, int64_t n, float* r, cudaStream_t s) {
+    if (n > 0) {
+        note_launch();
+        k_user_ratio<<<grid_for(n, 256, 65536), 256, 0, s>>>(tau, norm2, n, r);
+    }
+}
+
+void launch_item_uscore(const float* nrm_hi, int64_t m, const unsigned* ucum, int* uscore,
+                        cudaStream_t s) {
+    if (m > 0) {
+        note_launch();
+        k_item_uscore<<<grid_for(m, 256, 65536), 256, 0, s>>>(nrm_hi, m, ucum, uscore);
+    }
+}
+
+}  // namespace rkm
