@@ -274,6 +274,7 @@ rkm_status read_status(rkm_ctx* c, cudaStream_t s) {
     CUDA_TRY(cudaMemcpyAsync(c->st_host, c->st, sizeof(DevStatus), cudaMemcpyDeviceToHost, s));
     CUDA_TRY(cudaStreamSynchronize(s));
     collect_phases(c);
+    if (c->st_host->timeout) return fail(RKM_ETIMEOUT, "a bounded device wait gave up (kernel aborted)");
     return RKM_OK;
 }
 
@@ -358,15 +359,18 @@ rkm_status thresholds_core(rkm_ctx* c, const PathShape& ps, const float* U, int6
     }
     int cap = c->cand_cap;
     for (int attempt = 0;; ++attempt) {
+        const int nseg = ps.tc ? 2 : 1;
         Cand* cand;
         int *cand_cnt, *kid;
-        float* lfin;
+        unsigned* lfin;
         unsigned long long* keys;
-        TRY(c->ensure(c->cand, n * (int64_t)cap, &cand));
-        TRY(c->ensure(c->cand_cnt, n, &cand_cnt));
+        TRY(c->ensure(c->cand, n * (int64_t)nseg * cap, &cand));
+        TRY(c->ensure(c->cand_cnt, n * (int64_t)nseg, &cand_cnt));
         TRY(c->ensure(c->lfin, n, &lfin));
-        TRY(c->ensure(c->keys, n * (int64_t)cap, &keys));
-        TRY(c->ensure(c->kid, n * (int64_t)cap, &kid));
+        TRY(c->ensure(c->keys, n * (int64_t)nseg * cap, &keys));
+        TRY(c->ensure(c->kid, n * (int64_t)nseg * cap, &kid));
+        CUDA_TRY(cudaMemsetAsync(lfin, 0, n * sizeof(unsigned), s));
+        CUDA_TRY(cudaMemsetAsync(cand_cnt, 0, n * nseg * sizeof(int), s));
         ThresholdArgs a{};
         a.A = apack;
         a.B = it.pack;
@@ -381,7 +385,8 @@ rkm_status thresholds_core(rkm_ctx* c, const PathShape& ps, const float* U, int6
         a.eabs = ps.eabs;
         a.cand = cand;
         a.cand_cnt = cand_cnt;
-        a.lfin = lfin;
+        a.lfin_key = lfin;
+        a.nseg = nseg;
         a.st = c->st;
         a.num_sms = c->num_sms;
         {
@@ -398,14 +403,15 @@ rkm_status thresholds_core(rkm_ctx* c, const PathShape& ps, const float* U, int6
         {
             Phase ph(c, s, RKM_PHASE_EXACT);
             ExactData x{U, ldu, up.e, up.q, P, ldp, it.rp.e, it.rp.q, d, (int)round_up(d, 8), &c->st->grid_u};
-            launch_exact_tau(x, cand, cand_cnt, lfin, cap, it.perm, n, k, keys, kid, tau, tid, topk, c->st, s);
+            launch_exact_tau(x, cand, cand_cnt, lfin, cap, nseg, it.perm, n, k, keys, kid, tau, tid, topk, c->st,
+                             s);
         }
         TRY(read_status(c, s));
         if (!c->st_host->cand_overflow) break;
         if (cap >= it.m || attempt >= 3)
             return fail(RKM_EOVERFLOW, "candidate capacity %d overflowed after %d retries", cap, attempt);
         const int64_t next = std::min<int64_t>(it.m, (int64_t)cap * 4);
-        if ((double)n * next * 20.0 > 64e9)
+        if ((double)n * next * 20.0 * (ps.tc ? 2 : 1) > 64e9)
             return fail(RKM_EOVERFLOW, "candidate lists need more than 64 GB (n=%lld, cap=%lld)",
                         (long long)n, (long long)next);
         cap = (int)round_up(next, 32);

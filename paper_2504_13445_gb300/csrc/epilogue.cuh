@@ -39,7 +39,7 @@ __device__ __forceinline__ void heap_replace_root(float* heap, int t, int k, flo
     heap[j * BU + t] = v;
 }
 
-__device__ __noinline__ int compact_candidates(Cand* c, int cnt, float L) {
+static __device__ __noinline__ int compact_candidates(Cand* c, int cnt, float L) {
     int w = 0;
     for (int r = 0; r < cnt; ++r) {
         Cand x = c[r];

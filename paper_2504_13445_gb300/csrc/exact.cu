@@ -55,8 +55,15 @@ __device__ __forceinline__ double key_to_double(unsigned long long k) {
 }
 
 // One warp per user.
+__device__ __forceinline__ float key_to_float(unsigned k) {
+    if (k == 0u) return -INFINITY;
+    const unsigned b = (k & 0x80000000u) ? (k ^ 0x80000000u) : ~k;
+    return __uint_as_float(b);
+}
+
 __global__ void k_exact_tau(ExactData x, const Cand* __restrict__ cand, const int* __restrict__ cand_cnt,
-                            const float* __restrict__ lfin, int cap, const int* __restrict__ item_perm,
+                            const unsigned* __restrict__ lfin_key, int cap, int nseg,
+                            const int* __restrict__ item_perm,
                             int64_t n, int k, unsigned long long* __restrict__ keys,
                             int* __restrict__ kid, double* __restrict__ tau, int* __restrict__ tid,
                             int* __restrict__ topk, DevStatus* st) {
@@ -66,30 +73,32 @@ __global__ void k_exact_tau(ExactData x, const Cand* __restrict__ cand, const in
     const int64_t warps = ((int64_t)gridDim.x * blockDim.x) >> 5;
     unsigned long long kept_total = 0;
     for (int64_t u = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; u < n; u += warps) {
-        const float L = lfin[u];
-        const int cnt = cand_cnt[u];
-        const Cand* c = cand + u * (int64_t)cap;
-        unsigned long long* kk = keys + u * (int64_t)cap;
-        int* ki = kid + u * (int64_t)cap;
+        const float L = key_to_float(lfin_key[u]);
+        unsigned long long* kk = keys + u * (int64_t)nseg * cap;
+        int* ki = kid + u * (int64_t)nseg * cap;
         int kept = 0;
-        for (int base = 0; base < cnt; base += 32) {
-            const int j = base + lane;
-            bool keep = false;
-            Cand cj;
-            cj.ub = 0.f;
-            cj.pos = 0;
-            if (j < cnt) {
-                cj = c[j];
-                keep = cj.ub >= L;
+        for (int h = 0; h < nseg; ++h) {
+            const int cnt = cand_cnt[u * nseg + h];
+            const Cand* c = cand + (u * nseg + h) * (int64_t)cap;
+            for (int base = 0; base < cnt; base += 32) {
+                const int j = base + lane;
+                bool keep = false;
+                Cand cj;
+                cj.ub = 0.f;
+                cj.pos = 0;
+                if (j < cnt) {
+                    cj = c[j];
+                    keep = cj.ub >= L;
+                }
+                const unsigned mask = __ballot_sync(0xffffffffu, keep);
+                if (keep) {
+                    const int slot = kept + __popc(mask & lt_mask);
+                    const int io = item_perm[cj.pos];
+                    kk[slot] = double_key(exact_dot(x, grid, u, io));
+                    ki[slot] = io;
+                }
+                kept += __popc(mask);
             }
-            const unsigned mask = __ballot_sync(0xffffffffu, keep);
-            if (keep) {
-                const int slot = kept + __popc(mask & lt_mask);
-                const int io = item_perm[cj.pos];
-                kk[slot] = double_key(exact_dot(x, grid, u, io));
-                ki[slot] = io;
-            }
-            kept += __popc(mask);
         }
         __syncwarp();
         if (lane == 0) kept_total += (unsigned long long)kept;
@@ -150,14 +159,14 @@ __global__ void k_histogram(const int* __restrict__ topk, int64_t nk, int* __res
 
 }  // namespace
 
-void launch_exact_tau(const ExactData& x, const Cand* cand, const int* cand_cnt, const float* lfin, int cap,
-                      const int* item_perm, int64_t n, int k, unsigned long long* keys, int* kid,
+void launch_exact_tau(const ExactData& x, const Cand* cand, const int* cand_cnt, const unsigned* lfin_key,
+                      int cap, int nseg, const int* item_perm, int64_t n, int k, unsigned long long* keys, int* kid,
                       double* tau, int* tid, int* topk, DevStatus* st, cudaStream_t s) {
     if (n <= 0) return;
     int64_t blocks = (n * 32 + 255) / 256;
     if (blocks > 65536) blocks = 65536;
     note_launch();
-    k_exact_tau<<<(int)blocks, 256, 0, s>>>(x, cand, cand_cnt, lfin, cap, item_perm, n, k, keys, kid, tau,
+    k_exact_tau<<<(int)blocks, 256, 0, s>>>(x, cand, cand_cnt, lfin_key, cap, nseg, item_perm, n, k, keys, kid, tau,
                                             tid, topk, st);
 }
 

@@ -59,9 +59,10 @@ struct ThresholdArgs {
     const float* unrm;    // [n] ||u|| rounded up
     const float* tmax;    // [item tiles] max ||p|| of the tile, rounded up
     float coef, eabs;     // error bound E = coef*||u||*tmax + eabs
-    Cand* cand;           // [n][cap]
-    int* cand_cnt;        // [n]
-    float* lfin;          // [n] final lower threshold L_u
+    Cand* cand;           // [n][nseg][cap]
+    int* cand_cnt;        // [n][nseg]
+    unsigned* lfin_key;   // [n] float_key of the final lower threshold L_u (atomic max; 0 = none)
+    int nseg;             // candidate segments per user (epilogue groups of the kernel)
     DevStatus* st;
     int num_sms;
 };
@@ -83,8 +84,8 @@ struct ExactData {
 };
 
 // K3: exact tau_u, t_u and (optionally) S_k(u) from the candidate lists.
-void launch_exact_tau(const ExactData& x, const Cand* cand, const int* cand_cnt, const float* lfin,
-                      int cap, const int* item_perm, int64_t n, int k,
+void launch_exact_tau(const ExactData& x, const Cand* cand, const int* cand_cnt, const unsigned* lfin_key,
+                      int cap, int nseg, const int* item_perm, int64_t n, int k,
                       unsigned long long* keys, int* kid, double* tau, int* tid, int* topk,
                       DevStatus* st, cudaStream_t s);
 

@@ -116,7 +116,7 @@ __global__ void __launch_bounds__(SIMT_THREADS, 1) k_threshold_simt(ThresholdArg
             for (int j = 0; j < a.k; ++j) heap[j * BU + t] = -INFINITY;
             if (active) {
                 un = a.unrm[u];
-                mycand = a.cand + u * (int64_t)a.cap;
+                mycand = a.cand + u * (int64_t)a.nseg * a.cap;
             }
         }
         for (int64_t it = 0; it < item_tiles; ++it) {
@@ -135,8 +135,8 @@ __global__ void __launch_bounds__(SIMT_THREADS, 1) k_threshold_simt(ThresholdArg
             __syncthreads();
         }
         if (active) {
-            a.lfin[u] = s.L;
-            a.cand_cnt[u] = s.cnt;
+            atomicMax(&a.lfin_key[u], float_key(s.L));
+            a.cand_cnt[u * a.nseg] = s.cnt;
         }
     }
 }

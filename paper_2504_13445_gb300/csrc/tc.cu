@@ -1,20 +1,523 @@
-// Tensor-core (tcgen05) product kernels of the threshold and counting passes.
+// Tensor-core (tcgen05) product kernels of the threshold pass (K2) and the counting
+// pass (K5): BF16 operands staged by TMA into 128-byte-swizzled shared memory, one
+// thread issuing 128 x 256 x 16 MMAs into a double-buffered FP32 accumulator in TMEM
+// (2 x 256 columns), and eight epilogue warps that read the accumulator back with
+// tcgen05.ld and run the per-user epilogues of epilogue.cuh.  The user x item product
+// never leaves the SM.
+//
+// Roles (320 threads, one CTA per SM, persistent):
+//   warp 0      TMA producer: the resident operand once per work unit, then a ring of
+//               K-block slots of the streamed operand.
+//   warp 1      TMEM allocator and MMA issuer (one thread).
+//   warps 2-9   two epilogue warpgroups; group h consumes accumulator buffer h, i.e. every
+//               other product tile, so the epilogue runs two tiles at once.
+// Threshold pass: resident = 128 users, streamed = 256-item tiles.  Each warpgroup keeps
+// its own lower-bound heap per user (each is a valid lower bound of tau_u because it is the
+// k-th largest lower bound over a subset of the items); the final L_u is their maximum.
+// Counting pass: resident = 256 items, streamed = 128-user tiles of the unit's users.
 #include <cuda.h>
+#include <cudaTypedefs.h>
 #include <cuda_runtime.h>
 
 #include "common.cuh"
+#include "epilogue.cuh"
 #include "kernels.h"
+#include "tc_ptx.cuh"
 #include "tmap.h"
 
 namespace rkm {
 
-bool rkm_tc_available() { return false; }
+namespace {
 
-rkm_status make_tmaps(const void*, int64_t, const void*, int64_t, int, int, TmapPair*) {
-    return RKM_EINVAL;
+constexpr int TC_THREADS = 320;
+constexpr int MAX_SLOTS = 4;
+constexpr uint32_t TMEM_COLS = 512;
+constexpr uint32_t KB_BYTES_U = 128 * 128;  // one K-block (64 BF16) of 128 user rows
+constexpr uint32_t KB_BYTES_I = 256 * 128;  // one K-block of 256 item rows
+constexpr int SMEM_LIMIT = 232448;          // 227 KB opt-in maximum per block
+
+struct TcBars {
+    uint64_t res_full, res_empty, drain;
+    uint64_t full[MAX_SLOTS], empty[MAX_SLOTS];
+    uint64_t tfull[2], tempty[2];
+    uint32_t tmem_base;
+    int abort;
+};
+
+struct TcLayout {
+    uint32_t res_off, ring_off, aux_off, bar_off, bytes;
+    uint32_t slot_bytes;
+    int slots;
+};
+
+__device__ __forceinline__ uint8_t* align1024(uint8_t* raw) {
+    const uint32_t a = smem_u32(raw);
+    return raw + ((1024u - (a & 1023u)) & 1023u);
 }
 
-void launch_threshold_tc(const ThresholdArgs&, const void*, const void*, cudaStream_t) {}
-void launch_count_tc(const CountArgs&, const void*, const void*, cudaStream_t) {}
+// Bounded wait that ignores the abort flag (used to drain in-flight copies / MMAs at exit).
+__device__ __forceinline__ void drain_wait(uint64_t* bar, uint32_t parity, DevStatus* st) {
+    const long long t0 = clock64();
+    while (!mbar_try_wait(bar, parity)) {
+        if (clock64() - t0 > RKM_WAIT_CYCLES) {
+            st->timeout = 1u;
+            return;
+        }
+    }
+}
+
+__device__ __forceinline__ void setup(TcBars* B, int slots, int warp) {
+    if (threadIdx.x == 0) {
+        mbar_init(&B->res_full, 1);
+        mbar_init(&B->res_empty, 1);
+        mbar_init(&B->drain, 1);
+        for (int s = 0; s < slots; ++s) {
+            mbar_init(&B->full[s], 1);
+            mbar_init(&B->empty[s], 1);
+        }
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(&B->tfull[b], 1);
+            mbar_init(&B->tempty[b], 4);
+        }
+        B->abort = 0;
+        mbar_fence_init();
+    }
+    if (warp == 1) {
+        tmem_alloc(&B->tmem_base, TMEM_COLS);
+        tmem_relinquish();
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+}
+
+__device__ __forceinline__ void teardown(TcBars* B, int warp) {
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 1) {
+        __syncwarp();
+        tc_fence_after();
+        tmem_dealloc(B->tmem_base, TMEM_COLS);
+    }
+}
+
+// ---------------------------------------------------------------- K2
+
+__global__ void __launch_bounds__(TC_THREADS, 1)
+    k_threshold_tc(const ThresholdArgs a, const __grid_constant__ CUtensorMap tmA,
+                   const __grid_constant__ CUtensorMap tmB, const TcLayout L) {
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t* sm = align1024(smem_raw);
+    uint8_t* sA = sm + L.res_off;
+    uint8_t* ring = sm + L.ring_off;
+    float* heaps = reinterpret_cast<float*>(sm + L.aux_off);
+    TcBars* B = reinterpret_cast<TcBars*>(sm + L.bar_off);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int KB = a.dp >> 6;
+    const int S = L.slots;
+    const int64_t user_tiles = (a.n + BU - 1) / BU;
+    const int64_t item_tiles = (a.m + BI_TC - 1) / BI_TC;
+    volatile int* abort = &B->abort;
+
+    setup(B, S, warp);
+    const uint32_t tmem = B->tmem_base;
+
+    if (warp == 0) {
+        if (lane == 0) {
+            tma_prefetch_desc(&tmA);
+            tma_prefetch_desc(&tmB);
+            int slot = 0;
+            uint32_t ph = 0;
+            int issued[MAX_SLOTS] = {0, 0, 0, 0};
+            int res_loads = 0;
+            bool ok = true;
+            for (int64_t ut = blockIdx.x; ut < user_tiles && ok; ut += gridDim.x) {
+                if (res_loads > 0 && !mbar_wait(&B->res_empty, (res_loads - 1) & 1, abort, a.st)) break;
+                mbar_expect_tx(&B->res_full, KB * KB_BYTES_U);
+                for (int kb = 0; kb < KB; ++kb)
+                    tma_load_2d(sA + kb * KB_BYTES_U, &tmA, &B->res_full, kb * 64, (int)(ut * BU));
+                ++res_loads;
+                for (int64_t it = 0; it < item_tiles && ok; ++it) {
+                    for (int kb = 0; kb < KB; ++kb) {
+                        if (!mbar_wait(&B->empty[slot], ph ^ 1u, abort, a.st)) {
+                            ok = false;
+                            break;
+                        }
+                        mbar_expect_tx(&B->full[slot], KB_BYTES_I);
+                        tma_load_2d(ring + slot * KB_BYTES_I, &tmB, &B->full[slot], kb * 64, (int)(it * BI_TC));
+                        ++issued[slot];
+                        if (++slot == S) {
+                            slot = 0;
+                            ph ^= 1u;
+                        }
+                    }
+                }
+            }
+            // Copies in flight complete on their barriers; wait for them before the CTA exits.
+            for (int s = 0; s < S; ++s)
+                if (issued[s] > 0) drain_wait(&B->full[s], (uint32_t)(issued[s] - 1) & 1u, a.st);
+            if (res_loads > 0) drain_wait(&B->res_full, (uint32_t)(res_loads - 1) & 1u, a.st);
+        }
+    } else if (warp == 1) {
+        if (lane == 0) {
+            const uint32_t idesc = idesc_bf16_f32(BU, BI_TC);
+            int slot = 0;
+            uint32_t ph = 0, tile_j = 0;
+            int iter = 0;
+            bool ok = true;
+            for (int64_t ut = blockIdx.x; ut < user_tiles && ok; ut += gridDim.x, ++iter) {
+                if (!mbar_wait(&B->res_full, iter & 1, abort, a.st)) break;
+                tc_fence_after();
+                for (int64_t it = 0; it < item_tiles && ok; ++it) {
+                    const uint32_t b = tile_j & 1u, use = tile_j >> 1;
+                    if (!mbar_wait(&B->tempty[b], (use & 1u) ^ 1u, abort, a.st)) {
+                        ok = false;
+                        break;
+                    }
+                    tc_fence_after();
+                    const uint32_t d = tmem + b * BI_TC;
+                    for (int kb = 0; kb < KB; ++kb) {
+                        if (!mbar_wait(&B->full[slot], ph, abort, a.st)) {
+                            ok = false;
+                            break;
+                        }
+                        tc_fence_after();
+                        const uint64_t ad = sdesc_sw128(smem_u32(sA + kb * KB_BYTES_U));
+                        const uint64_t bd = sdesc_sw128(smem_u32(ring + slot * KB_BYTES_I));
+#pragma unroll
+                        for (int k = 0; k < 4; ++k)
+                            tc_mma_bf16(d, ad + 2u * k, bd + 2u * k, idesc, (kb | k) != 0 ? 1u : 0u);
+                        tc_commit(&B->empty[slot]);
+                        if (++slot == S) {
+                            slot = 0;
+                            ph ^= 1u;
+                        }
+                    }
+                    if (!ok) break;
+                    tc_commit(&B->tfull[b]);
+                    ++tile_j;
+                }
+                if (!ok) break;
+                tc_commit(&B->res_empty);
+            }
+            tc_commit(&B->drain);
+            drain_wait(&B->drain, 0u, a.st);
+        }
+    } else {
+        const int ew = warp - 2;          // 0..7
+        const int h = ew >> 2;            // warpgroup = accumulator buffer it consumes
+        const int q = warp & 3;           // TMEM lane quarter this warp may access
+        const int r = q * 32 + lane;      // user row of the tile
+        float* heap = heaps + h * (a.k * BU);
+        uint32_t tile_j = 0;
+        bool ok = true;
+        for (int64_t ut = blockIdx.x; ut < user_tiles && ok; ut += gridDim.x) {
+            const int64_t u = ut * BU + r;
+            const bool active = u < a.n;
+            for (int j = 0; j < a.k; ++j) heap[j * BU + r] = -INFINITY;
+            SelState s;
+            s.L = -INFINITY;
+            s.thr = -INFINITY;
+            s.cnt = 0;
+            const float un = active ? a.unrm[u] : 0.f;
+            Cand* mycand = a.cand + ((active ? u : 0) * a.nseg + h) * (int64_t)a.cap;
+            for (int64_t it = 0; it < item_tiles; ++it) {
+                const uint32_t b = tile_j & 1u, use = tile_j >> 1;
+                ++tile_j;
+                if ((int)b != h) continue;
+                if (!mbar_wait(&B->tfull[b], use & 1u, abort, a.st)) {
+                    ok = false;
+                    break;
+                }
+                __syncwarp();
+                tc_fence_after();
+                const float E = err_bound(a.coef, a.eabs, un, a.tmax[it]);
+                s.thr = __fsub_rd(s.L, E);
+                const uint32_t tb = tmem + ((uint32_t)(q * 32) << 16) + b * BI_TC;
+#pragma unroll 1
+                for (int c0 = 0; c0 < BI_TC; c0 += 32) {
+                    float v[32];
+                    __syncwarp();
+                    tmem_ld32(tb + c0, v);
+                    sel_chunk(v, active, (int)(it * BI_TC + c0), a.m, E, s, mycand, a.cap, heap, r, a.k, a.st);
+                }
+                tc_fence_before();
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&B->tempty[b]);
+            }
+            if (active) {
+                atomicMax(&a.lfin_key[u], float_key(s.L));
+                a.cand_cnt[u * a.nseg + h] = s.cnt;
+            }
+        }
+    }
+    teardown(B, warp);
+}
+
+// ---------------------------------------------------------------- K5
+
+__device__ __forceinline__ void decode_unit(const CountArgs& a, unsigned w, int len, int& T, int64_t& ut0,
+                                            int64_t& ut1) {
+    int lo = 0, hi = len;
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (a.unit_off[mid] <= w) lo = mid; else hi = mid;
+    }
+    T = a.t_begin + lo;
+    const int g = (int)(w - a.unit_off[lo]);
+    const int64_t nT = a.nprefix[T];
+    const int64_t all = (nT + BU - 1) / BU;
+    ut0 = (int64_t)g * a.group;
+    ut1 = ut0 + a.group;
+    if (ut1 > all) ut1 = all;
+}
+
+__global__ void __launch_bounds__(TC_THREADS, 1)
+    k_count_tc(const CountArgs a, const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
+               const TcLayout L) {
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t* sm = align1024(smem_raw);
+    uint8_t* sB = sm + L.res_off;
+    uint8_t* ring = sm + L.ring_off;
+    int* cnt_all = reinterpret_cast<int*>(sm + L.aux_off);
+    TcBars* B = reinterpret_cast<TcBars*>(sm + L.bar_off);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int KB = a.dp >> 6;
+    const int S = L.slots;
+    const unsigned total = a.st->units_total;
+    const int len = a.st->t_end - a.t_begin;
+    volatile int* abort = &B->abort;
+
+    setup(B, S, warp);
+    const uint32_t tmem = B->tmem_base;
+
+    if (warp == 0) {
+        if (lane == 0) {
+            tma_prefetch_desc(&tmA);
+            tma_prefetch_desc(&tmB);
+            int slot = 0;
+            uint32_t ph = 0;
+            int issued[MAX_SLOTS] = {0, 0, 0, 0};
+            int res_loads = 0;
+            bool ok = true;
+            unsigned long long pairs = 0;
+            for (unsigned w = blockIdx.x; w < total && ok; w += gridDim.x) {
+                int T;
+                int64_t ut0, ut1;
+                decode_unit(a, w, len, T, ut0, ut1);
+                if (res_loads > 0 && !mbar_wait(&B->res_empty, (res_loads - 1) & 1, abort, a.st)) break;
+                mbar_expect_tx(&B->res_full, KB * KB_BYTES_I);
+                for (int kb = 0; kb < KB; ++kb)
+                    tma_load_2d(sB + kb * KB_BYTES_I, &tmB, &B->res_full, kb * 64, T * BI_TC);
+                ++res_loads;
+                for (int64_t ut = ut0; ut < ut1 && ok; ++ut) {
+                    for (int kb = 0; kb < KB; ++kb) {
+                        if (!mbar_wait(&B->empty[slot], ph ^ 1u, abort, a.st)) {
+                            ok = false;
+                            break;
+                        }
+                        mbar_expect_tx(&B->full[slot], KB_BYTES_U);
+                        tma_load_2d(ring + slot * KB_BYTES_U, &tmA, &B->full[slot], kb * 64, (int)(ut * BU));
+                        ++issued[slot];
+                        if (++slot == S) {
+                            slot = 0;
+                            ph ^= 1u;
+                        }
+                    }
+                }
+                const int64_t uend = (ut1 * BU < a.n) ? ut1 * BU : a.n;
+                if (ut1 > ut0) pairs += (unsigned long long)(uend - ut0 * BU) * BI_TC;
+            }
+            if (pairs) atomicAdd(&a.st->pairs_evaluated, pairs);
+            for (int s = 0; s < S; ++s)
+                if (issued[s] > 0) drain_wait(&B->full[s], (uint32_t)(issued[s] - 1) & 1u, a.st);
+            if (res_loads > 0) drain_wait(&B->res_full, (uint32_t)(res_loads - 1) & 1u, a.st);
+        }
+    } else if (warp == 1) {
+        if (lane == 0) {
+            const uint32_t idesc = idesc_bf16_f32(BU, BI_TC);
+            int slot = 0;
+            uint32_t ph = 0, tile_j = 0;
+            int iter = 0;
+            bool ok = true;
+            for (unsigned w = blockIdx.x; w < total && ok; w += gridDim.x, ++iter) {
+                int T;
+                int64_t ut0, ut1;
+                decode_unit(a, w, len, T, ut0, ut1);
+                if (!mbar_wait(&B->res_full, iter & 1, abort, a.st)) break;
+                tc_fence_after();
+                for (int64_t ut = ut0; ut < ut1 && ok; ++ut) {
+                    const uint32_t b = tile_j & 1u, use = tile_j >> 1;
+                    if (!mbar_wait(&B->tempty[b], (use & 1u) ^ 1u, abort, a.st)) {
+                        ok = false;
+                        break;
+                    }
+                    tc_fence_after();
+                    const uint32_t d = tmem + b * BI_TC;
+                    for (int kb = 0; kb < KB; ++kb) {
+                        if (!mbar_wait(&B->full[slot], ph, abort, a.st)) {
+                            ok = false;
+                            break;
+                        }
+                        tc_fence_after();
+                        const uint64_t ad = sdesc_sw128(smem_u32(ring + slot * KB_BYTES_U));
+                        const uint64_t bd = sdesc_sw128(smem_u32(sB + kb * KB_BYTES_I));
+#pragma unroll
+                        for (int k = 0; k < 4; ++k)
+                            tc_mma_bf16(d, ad + 2u * k, bd + 2u * k, idesc, (kb | k) != 0 ? 1u : 0u);
+                        tc_commit(&B->empty[slot]);
+                        if (++slot == S) {
+                            slot = 0;
+                            ph ^= 1u;
+                        }
+                    }
+                    if (!ok) break;
+                    tc_commit(&B->tfull[b]);
+                    ++tile_j;
+                }
+                if (!ok) break;
+                tc_commit(&B->res_empty);
+            }
+            tc_commit(&B->drain);
+            drain_wait(&B->drain, 0u, a.st);
+        }
+    } else {
+        const int ew = warp - 2;
+        const int h = ew >> 2;
+        const int q = warp & 3;
+        const int r = q * 32 + lane;
+        int* cw = cnt_all + ew * BI_TC;  // this warp's per-item member counters
+        for (int c = lane; c < BI_TC; c += 32) cw[c] = 0;
+        __syncwarp();
+        uint32_t tile_j = 0;
+        bool ok = true;
+        for (unsigned w = blockIdx.x; w < total && ok; w += gridDim.x) {
+            int T;
+            int64_t ut0, ut1;
+            decode_unit(a, w, len, T, ut0, ut1);
+            const float pn = a.tmax[T];
+            const int pos0 = T * BI_TC;
+            for (int64_t ut = ut0; ut < ut1; ++ut) {
+                const uint32_t b = tile_j & 1u, use = tile_j >> 1;
+                ++tile_j;
+                if ((int)b != h) continue;
+                if (!mbar_wait(&B->tfull[b], use & 1u, abort, a.st)) {
+                    ok = false;
+                    break;
+                }
+                __syncwarp();
+                tc_fence_after();
+                const int64_t us = ut * BU + r;
+                const bool active = us < a.n;
+                float hi_t = 0.f, lo_t = 0.f;
+                int u_orig = 0;
+                if (active) {
+                    const float E = err_bound(a.coef, a.eabs, a.unrm_s[us], pn);
+                    const double tau = a.tau_s[us];
+                    hi_t = __fadd_ru(__double2float_ru(tau), E);
+                    lo_t = __fsub_rd(__double2float_rd(tau), E);
+                    u_orig = a.uperm[us];
+                }
+                const uint32_t tb = tmem + ((uint32_t)(q * 32) << 16) + b * BI_TC;
+#pragma unroll 1
+                for (int c0 = 0; c0 < BI_TC; c0 += 32) {
+                    float v[32];
+                    __syncwarp();
+                    tmem_ld32(tb + c0, v);
+                    count_chunk(v, active, c0, pos0 + c0, a.m, hi_t, lo_t, cw, u_orig, a.band, a.band_cap, a.st);
+                }
+                tc_fence_before();
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&B->tempty[b]);
+            }
+            __syncwarp();
+            for (int c = lane; c < BI_TC; c += 32) {
+                const int x = cw[c];
+                if (x != 0) {
+                    if (pos0 + c < a.m) atomicAdd(&a.counts[pos0 + c], x);
+                    cw[c] = 0;
+                }
+            }
+            __syncwarp();
+        }
+    }
+    teardown(B, warp);
+}
+
+TcLayout make_layout(uint32_t res_bytes, uint32_t slot_bytes, uint32_t aux_bytes, int max_slots) {
+    TcLayout L{};
+    L.res_off = 0;
+    L.ring_off = res_bytes;
+    L.slot_bytes = slot_bytes;
+    aux_bytes = (aux_bytes + 1023u) & ~1023u;
+    const uint32_t fixed = 1024u + res_bytes + aux_bytes + 1024u;  // align slack + barriers
+    int slots = max_slots;
+    while (slots > 1 && fixed + slots * slot_bytes > (uint32_t)SMEM_LIMIT) --slots;
+    L.slots = slots;
+    L.aux_off = L.ring_off + slots * slot_bytes;
+    L.bar_off = L.aux_off + aux_bytes;
+    L.bytes = 1024u + L.bar_off + (uint32_t)sizeof(TcBars);
+    return L;
+}
+
+PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    if (!fn) {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+    }
+    return fn;
+}
+
+bool encode_bf16(CUtensorMap* map, const void* base, int64_t rows, int dp, int box_rows) {
+    auto fn = encode_fn();
+    if (!fn) return false;
+    cuuint64_t dims[2] = {(cuuint64_t)dp, (cuuint64_t)rows};
+    cuuint64_t strides[1] = {(cuuint64_t)dp * 2u};
+    cuuint32_t box[2] = {64u, (cuuint32_t)box_rows};
+    cuuint32_t estr[2] = {1u, 1u};
+    CUresult r = fn(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(base), dims, strides, box, estr,
+                    CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                    CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS;
+}
+
+}  // namespace
+
+bool rkm_tc_available() { return true; }
+
+rkm_status make_tmaps(const void* A, int64_t a_rows, const void* B, int64_t b_rows, int dp, int item_tile,
+                      TmapPair* out) {
+    if (dp % 64 != 0 || a_rows % BU != 0 || b_rows % item_tile != 0 || item_tile != BI_TC) return RKM_EINVAL;
+    if ((reinterpret_cast<uintptr_t>(A) & 15u) || (reinterpret_cast<uintptr_t>(B) & 15u)) return RKM_EINVAL;
+    if (!encode_bf16(&out->a, A, a_rows, dp, BU)) return RKM_ECUDA;
+    if (!encode_bf16(&out->b, B, b_rows, dp, item_tile)) return RKM_ECUDA;
+    return RKM_OK;
+}
+
+void launch_threshold_tc(const ThresholdArgs& a, const void* tmapA, const void* tmapB, cudaStream_t s) {
+    const int KB = a.dp / 64;
+    const TcLayout L = make_layout(KB * KB_BYTES_U, KB_BYTES_I, 2u * BU * a.k * 4u, MAX_SLOTS);
+    cudaFuncSetAttribute(k_threshold_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.bytes);
+    const int64_t user_tiles = (a.n + BU - 1) / BU;
+    const int grid = (int)(user_tiles < a.num_sms ? user_tiles : a.num_sms);
+    if (grid < 1) return;
+    note_launch();
+    k_threshold_tc<<<grid, TC_THREADS, L.bytes, s>>>(a, *static_cast<const CUtensorMap*>(tmapA),
+                                                      *static_cast<const CUtensorMap*>(tmapB), L);
+}
+
+void launch_count_tc(const CountArgs& a, const void* tmapA, const void* tmapB, cudaStream_t s) {
+    const int KB = a.dp / 64;
+    const TcLayout L = make_layout(KB * KB_BYTES_I, KB_BYTES_U, 8u * BI_TC * 4u, MAX_SLOTS);
+    cudaFuncSetAttribute(k_count_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.bytes);
+    note_launch();
+    k_count_tc<<<a.num_sms, TC_THREADS, L.bytes, s>>>(a, *static_cast<const CUtensorMap*>(tmapA),
+                                                      *static_cast<const CUtensorMap*>(tmapB), L);
+}
 
 }  // namespace rkm
