@@ -42,6 +42,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--n", type=int, default=None, help="override the number of users (profiling cases)")
+    ap.add_argument("--m", type=int, default=None, help="override the number of items (profiling cases)")
     return ap.parse_args()
 
 
@@ -142,21 +144,21 @@ def fp32_alu_peak_tflops(sm_mhz: float, sms: int = 152) -> float:
     return sms * 128 * 2 * sm_mhz * 1e6 / 1e12
 
 
-def cpu_baseline(W, workload: str, seconds: float) -> dict:
+def cpu_baseline(W, workload: str, seconds: float, n=None, m=None) -> dict:
     """The oracle as it stands on the host cores, on users [0, S) of the workload against
     every item (Definition 1 thresholds and the histogram of S_k(u)), S grown in blocks
     until about `seconds` of work.  Runs in a spawned child so BLAS threads are pinned."""
     import multiprocessing as mp
     ctx = mp.get_context("spawn")
     q = ctx.Queue()
-    p = ctx.Process(target=_cpu_child, args=(workload, W.k, seconds, q))
+    p = ctx.Process(target=_cpu_child, args=(workload, W.k, seconds, q, n, m))
     p.start()
     res = q.get()
     p.join()
     return res
 
 
-def _cpu_child(cfg, k, seconds, q):
+def _cpu_child(cfg, k, seconds, q, n=None, m=None):
     threads = os.cpu_count() or 1
     os.environ["OPENBLAS_NUM_THREADS"] = "1"
     os.environ["OMP_NUM_THREADS"] = "1"
@@ -165,7 +167,8 @@ def _cpu_child(cfg, k, seconds, q):
     import numpy as np  # noqa: F401
     import oracle
     import workloads
-    W = workloads.make(cfg)
+    over = {key: v for key, v in (("n", n), ("m", m)) if v}
+    W = workloads.make(cfg, **over)
     block = 64 * threads
     t0 = time.perf_counter()
     done = 0
@@ -188,7 +191,7 @@ def run_reference(args, rank, world):
     import oracle
     import workloads
     threads = os.cpu_count() or 1
-    W = workloads.make(args.workload)
+    W = workload(args)
     sample = 32 * threads
     times = []
     for step in range(args.warmup + args.steps):
@@ -212,6 +215,16 @@ def run_reference(args, rank, world):
     print(json.dumps(line), flush=True)
 
 
+def workload(args):
+    import workloads
+    over = {}
+    if args.n:
+        over["n"] = args.n
+    if args.m:
+        over["m"] = args.m
+    return workloads.make(args.workload, **over)
+
+
 def run_ours(args, rank, local, world):
     import numpy as np
     import torch
@@ -222,7 +235,7 @@ def run_ours(args, rank, local, world):
     import workloads
 
     torch.cuda.set_device(local)
-    W = workloads.make(args.workload)
+    W = workload(args)
     U = torch.from_numpy(W.U).cuda()
     P = torch.from_numpy(W.P).cuda()
     flush = torch.empty(512 << 20, dtype=torch.uint8, device="cuda")
@@ -301,7 +314,8 @@ def run_ours(args, rank, local, world):
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "bf16" if args.precision == "bf16" else "f32",
             "data": "synthetic",
-            "config": {"workload": args.workload, "n": W.n, "m": W.m, "d": W.d, "k": W.k, "N": W.N,
+            "config": {"workload": args.workload if not (args.n or args.m) else f"{args.workload} resized",
+                       "n": W.n, "m": W.m, "d": W.d, "k": W.k, "N": W.N,
                        "precision": args.precision, "inputs": "FP32 on the 2^-12 grid, MF-like",
                        "l2": "flushed (512 MiB write) before each timed step",
                        "parallelism": "replicas" if world > 1 else "single GPU"},
@@ -313,7 +327,7 @@ def run_ours(args, rank, local, world):
     if e2e:
         line["e2e"] = e2e
     if not args.no_cpu_baseline and world == 1:
-        line["cpu_baseline"] = cpu_baseline(W, args.workload, args.cpu_seconds)
+        line["cpu_baseline"] = cpu_baseline(W, args.workload, args.cpu_seconds, args.n, args.m)
     print(json.dumps(line), flush=True)
 
 

@@ -73,25 +73,25 @@ struct rkm_ctx {
     DevStatus* st = nullptr;     // device status word
     DevStatus* st_host = nullptr;  // pinned mirror
     // users (original order)
-    Buf u_e, u_q, u_n2, u_nrm, u_pack;
+    Buf u_e, u_q, u_n2, u_nrm, u_nhat, u_del, u_pack;
     // items (original order; sorted copies)
-    Buf p_e, p_q, p_n2, p_nrm, p_perm, p_nrm_s, p_pack, tmax;
+    Buf p_e, p_q, p_n2, p_nrm, p_nhat, p_del, p_perm, p_pack, tmax, thmax, tdel;
     // bucket sort scratch
     Buf hist, offs;
     // threshold pass
     Buf cand, cand_cnt, lfin, keys, kid;
     // counting pass
-    Buf r_u, uperm, ucum, us_pack, us_nrm, us_tau, us_tid, nprefix, unit_off, band, cnt_s, top_ids,
-        top_sc, tau_tmp, tid_tmp;
+    Buf r_u, uperm, ucum, us_pack, us_nrm, us_nhat, us_del, us_tau, us_tid, nprefix, unit_off, band, cnt_s,
+        top_ids, top_sc, tau_tmp, tid_tmp;
     // serving (resident users)
     bool resident = false;
     int64_t res_n = 0;
     int res_d = 0;
     unsigned res_grid = 0;
-    Buf res_U, res_e, res_q, res_tau, res_tid, res_uperm, res_ucum, res_pack, res_nrm_s, res_tau_s,
-        res_tid_s;
+    Buf res_U, res_e, res_q, res_tau, res_tid, res_uperm, res_ucum, res_pack, res_nrm_s, res_nhat_s,
+        res_del_s, res_tau_s, res_tid_s;
     // query scratch
-    Buf q_e, q_q, q_n2, q_nrm, q_perm, q_nrm_s, q_pack, q_tmax, q_cnt;
+    Buf q_e, q_q, q_n2, q_nrm, q_nhat, q_del, q_perm, q_pack, q_tmax, q_thmax, q_tdel, q_cnt;
     // host staging for rkm_topn_host
     Buf h_U, h_P, h_ids, h_sc;
     int cand_cap = 0;
@@ -137,13 +137,14 @@ struct rkm_ctx {
     }
 
     void free_all() {
-        Buf* all[] = {&u_e, &u_q, &u_n2, &u_nrm, &u_pack, &p_e, &p_q, &p_n2, &p_nrm, &p_perm, &p_nrm_s,
-                      &p_pack, &tmax, &hist, &offs, &cand, &cand_cnt, &lfin, &keys, &kid, &r_u, &uperm,
-                      &ucum, &us_pack, &us_nrm, &us_tau, &us_tid, &nprefix, &unit_off, &band, &cnt_s,
-                      &top_ids, &top_sc, &tau_tmp, &tid_tmp, &res_U, &res_e, &res_q, &res_tau, &res_tid,
-                      &res_uperm, &res_ucum, &res_pack, &res_nrm_s, &res_tau_s, &res_tid_s, &q_e, &q_q,
-                      &q_n2, &q_nrm, &q_perm, &q_nrm_s, &q_pack, &q_tmax, &q_cnt, &h_U, &h_P, &h_ids,
-                      &h_sc};
+        Buf* all[] = {&u_e, &u_q, &u_n2, &u_nrm, &u_nhat, &u_del, &u_pack, &p_e, &p_q, &p_n2, &p_nrm,
+                      &p_nhat, &p_del, &p_perm, &p_pack, &tmax, &thmax, &tdel, &hist, &offs, &cand,
+                      &cand_cnt, &lfin, &keys, &kid, &r_u, &uperm, &ucum, &us_pack, &us_nrm, &us_nhat,
+                      &us_del, &us_tau, &us_tid, &nprefix, &unit_off, &band, &cnt_s, &top_ids, &top_sc,
+                      &tau_tmp, &tid_tmp, &res_U, &res_e, &res_q, &res_tau, &res_tid, &res_uperm, &res_ucum,
+                      &res_pack, &res_nrm_s, &res_nhat_s, &res_del_s, &res_tau_s, &res_tid_s, &q_e, &q_q,
+                      &q_n2, &q_nrm, &q_nhat, &q_del, &q_perm, &q_pack, &q_tmax, &q_thmax, &q_tdel, &q_cnt,
+                      &h_U, &h_P, &h_ids, &h_sc};
         for (Buf* b : all) {
             if (b->p) cudaFree(b->p);
             b->p = nullptr;
@@ -209,19 +210,20 @@ struct PathShape {
     bool tc;        // tensor-core kernels
     int item_tile;  // BI of the product kernels
     int dp;         // padded depth (elements)
-    float coef, eabs;
+    float cacc, eabs;
 };
 
-// Error bound of the approximate products.  Representation error of the operands
-// (unit roundoff u, round to nearest) gives |sum xh*yh - sum x*y| <= (2u + u^2) sum|x y|;
-// accumulation adds c_acc * sum|xh yh| <= c_acc (1+u)^2 sum|x y|, and sum|x y| <= ||x|| ||y||.
-// FP32 CUDA cores: sequential FMA, gamma_d = d 2^-24 / (1 - d 2^-24) (u = 0 for the
-// operands), doubled.  Tensor cores: products of BF16 operands are exact in FP32; the
-// FP32 accumulation order and rounding of the tensor core are not specified, so c_acc is
-// set to d 2^-22, four times gamma_d (truncating accumulation, as measured by Fasi,
-// Higham, Mikaitis and Pranesh, PeerJ Comput. Sci. 2021, needs at most twice gamma_d).
-// A d 2^-50 term covers the gap between the FP64 reference sum and the exact value for
-// off-grid inputs; eabs covers FP32 underflow of products.
+// Error bound of the approximate products (err_bound in common.cuh):
+//   |v - u.p| <= ||u^ - u|| ||p^|| + ||u|| ||p^ - p|| + cacc ||u^|| ||p^|| + eabs,
+// where u^, p^ are the operands the product kernel multiplies exactly (BF16 products are
+// exact in FP32; FP32 operands are used as they are) and cacc bounds the accumulation.
+// FP32 CUDA cores: sequential FMA, so the accumulation error is at most gamma_d sum|u^ p^|,
+// gamma_d = d 2^-24 / (1 - d 2^-24) (Higham, "Accuracy and Stability of Numerical
+// Algorithms", Section 3.1); cacc = 2 gamma_d.  Tensor cores: the order and rounding of the
+// FP32 accumulation are not specified; cacc = d 2^-22, four times gamma_d (measured tensor-core
+// accumulation truncates, Fasi, Higham, Mikaitis and Pranesh, PeerJ Comput. Sci. 2021, which
+// needs at most twice gamma_d).  A further d 2^-50 covers the gap between the FP64 reference
+// sum and the exact value for off-grid inputs; eabs covers FP32 underflow of products.
 PathShape path_shape(rkm_precision prec, int d) {
     PathShape ps{};
     const double dd = (double)d;
@@ -230,16 +232,14 @@ PathShape path_shape(rkm_precision prec, int d) {
         ps.tc = false;
         ps.item_tile = BI_SIMT;
         ps.dp = (int)round_up(d, 32);
-        ps.coef = (float)((2.0 * g32 + dd * 0x1p-50) * (1.0 + 0x1p-20));
+        ps.cacc = (float)((2.0 * g32 + dd * 0x1p-50) * (1.0 + 0x1p-20));
     } else {
         ps.tc = true;
         ps.item_tile = BI_TC;
         ps.dp = (int)round_up(d, 64);
-        const double u = 0x1p-8;
-        const double cacc = dd * 0x1p-22;
-        ps.coef = (float)(((2.0 * u + u * u) + cacc * (1.0 + u) * (1.0 + u) + dd * 0x1p-50) * (1.0 + 0x1p-20));
+        ps.cacc = (float)((dd * 0x1p-22 + dd * 0x1p-50) * (1.0 + 0x1p-20));
     }
-    ps.coef = nextafterf(ps.coef, INFINITY);
+    ps.cacc = nextafterf(ps.cacc, INFINITY);
     ps.eabs = (float)(dd * 0x1p-126);
     return ps;
 }
@@ -288,17 +288,22 @@ struct RowPrep {
     int* e;
     int16_t* q;
     double* n2;
-    float* nrm;
+    float* nrm;   // ||x|| rounded up
+    float* nhat;  // ||x^|| rounded up (x^ = operand of the product kernels)
+    float* del;   // ||x^ - x|| rounded up
 };
 
-rkm_status prep_rows(rkm_ctx* c, const float* X, int64_t rows, int64_t ld, int d, Buf& be, Buf& bq,
-                     Buf& bn2, Buf& bnrm, RowPrep* out, cudaStream_t s) {
+rkm_status prep_rows(rkm_ctx* c, const PathShape& ps, const float* X, int64_t rows, int64_t ld, int d, Buf& be,
+                     Buf& bq, Buf& bn2, Buf& bnrm, Buf& bnhat, Buf& bdel, RowPrep* out, cudaStream_t s) {
     const int dq = (int)round_up(d, 8);
     TRY(c->ensure(be, rows, &out->e));
     TRY(c->ensure(bq, rows * dq, &out->q));
     TRY(c->ensure(bn2, rows, &out->n2));
     TRY(c->ensure(bnrm, rows, &out->nrm));
-    launch_prep_rows(X, rows, ld, d, out->e, out->q, dq, out->n2, out->nrm, &c->st->grid_u, s);
+    TRY(c->ensure(bnhat, rows, &out->nhat));
+    TRY(c->ensure(bdel, rows, &out->del));
+    launch_prep_rows(X, rows, ld, d, out->e, out->q, dq, out->n2, out->nrm, out->nhat, out->del, ps.tc,
+                     &c->st->grid_u, s);
     return RKM_OK;
 }
 
@@ -323,29 +328,45 @@ struct ItemSide {
     RowPrep rp;
     int* perm;       // sorted pos -> original id
     void* pack;      // [m_pad][dp]
-    float* tmax;     // [tiles]
+    float* tmax;     // [tiles] max ||p||
+    float* thmax;    // [tiles] max ||p^||
+    float* tdel;     // [tiles] max ||p^ - p||
     int64_t m, m_pad, tiles;
 };
 
+struct ItemBufs {
+    Buf &e, &q, &n2, &nrm, &nhat, &del, &perm, &pack, &tmax, &thmax, &tdel;
+};
+
 rkm_status prep_items(rkm_ctx* c, const PathShape& ps, const float* P, int64_t m, int64_t ldp, int d,
-                      Buf& be, Buf& bq, Buf& bn2, Buf& bnrm, Buf& bperm, Buf& bnrm_s, Buf& bpack,
-                      Buf& btmax, ItemSide* it, cudaStream_t s) {
+                      const ItemBufs& bb, ItemSide* it, cudaStream_t s) {
     it->m = m;
     it->m_pad = round_up(std::max<int64_t>(m, 1), BI_TC);
     it->tiles = (m + ps.item_tile - 1) / ps.item_tile;
-    TRY(prep_rows(c, P, m, ldp, d, be, bq, bn2, bnrm, &it->rp, s));
+    TRY(prep_rows(c, ps, P, m, ldp, d, bb.e, bb.q, bb.n2, bb.nrm, bb.nhat, bb.del, &it->rp, s));
     unsigned *hist, *offs;
     TRY(c->ensure(c->hist, NBUCKET, &hist));
     TRY(c->ensure(c->offs, NBUCKET, &offs));
-    TRY(c->ensure(bperm, m, &it->perm));
+    TRY(c->ensure(bb.perm, m, &it->perm));
     launch_bucket_sort(it->rp.nrm, m, true, hist, offs, it->perm, nullptr, s);
-    TRY(pack(c, ps, P, m, ldp, d, it->perm, it->m_pad, bpack, &it->pack, s));
-    float* nrm_s;
-    TRY(c->ensure(bnrm_s, m, &nrm_s));
-    launch_gather_f32(it->rp.nrm, it->perm, m, nrm_s, s);
-    TRY(c->ensure(btmax, std::max<int64_t>(it->tiles, 1), &it->tmax));
-    launch_tile_max(nrm_s, m, ps.item_tile, it->tiles, it->tmax, s);
+    TRY(pack(c, ps, P, m, ldp, d, it->perm, it->m_pad, bb.pack, &it->pack, s));
+    const int64_t nt = std::max<int64_t>(it->tiles, 1);
+    TRY(c->ensure(bb.tmax, nt, &it->tmax));
+    TRY(c->ensure(bb.thmax, nt, &it->thmax));
+    TRY(c->ensure(bb.tdel, nt, &it->tdel));
+    launch_tile_max(it->rp.nrm, it->rp.nhat, it->rp.del, it->perm, m, ps.item_tile, it->tiles, it->tmax,
+                    it->thmax, it->tdel, s);
     return RKM_OK;
+}
+
+ItemBufs catalogue_bufs(rkm_ctx* c) {
+    return ItemBufs{c->p_e, c->p_q, c->p_n2, c->p_nrm, c->p_nhat, c->p_del, c->p_perm, c->p_pack, c->tmax,
+                    c->thmax, c->tdel};
+}
+
+ItemBufs query_bufs(rkm_ctx* c) {
+    return ItemBufs{c->q_e, c->q_q, c->q_n2, c->q_nrm, c->q_nhat, c->q_del, c->q_perm, c->q_pack, c->q_tmax,
+                    c->q_thmax, c->q_tdel};
 }
 
 rkm_status thresholds_core(rkm_ctx* c, const PathShape& ps, const float* U, int64_t n, int64_t ldu,
@@ -380,8 +401,12 @@ rkm_status thresholds_core(rkm_ctx* c, const PathShape& ps, const float* U, int6
         a.k = k;
         a.cap = cap;
         a.unrm = up.nrm;
+        a.unhat = up.nhat;
+        a.udel = up.del;
         a.tmax = it.tmax;
-        a.coef = ps.coef;
+        a.thmax = it.thmax;
+        a.tdel = it.tdel;
+        a.cacc = ps.cacc;
         a.eabs = ps.eabs;
         a.cand = cand;
         a.cand_cnt = cand_cnt;
@@ -433,28 +458,38 @@ struct UserOrder {
     unsigned* ucum;
     void* pack;
     float* nrm_s;
+    float* nhat_s;
+    float* del_s;
     double* tau_s;
     int* tid_s;
 };
 
+struct UserBufs {
+    Buf &perm, &cum, &pack, &nrm, &nhat, &del, &tau, &tid;
+};
+
 rkm_status order_users(rkm_ctx* c, const PathShape& ps, const float* U, int64_t n, int64_t ldu, int d,
-                       const RowPrep& up, const double* tau, const int* tid, Buf& bperm, Buf& bcum,
-                       Buf& bpack, Buf& bnrm, Buf& btau, Buf& btid, UserOrder* uo, cudaStream_t s) {
+                       const RowPrep& up, const double* tau, const int* tid, const UserBufs& bb, UserOrder* uo,
+                       cudaStream_t s) {
     float* r;
     unsigned *hist, *offs;
     TRY(c->ensure(c->r_u, n, &r));
     TRY(c->ensure(c->hist, NBUCKET, &hist));
     TRY(c->ensure(c->offs, NBUCKET, &offs));
-    TRY(c->ensure(bperm, n, &uo->uperm));
-    TRY(c->ensure(bcum, NBUCKET, &uo->ucum));
+    TRY(c->ensure(bb.perm, n, &uo->uperm));
+    TRY(c->ensure(bb.cum, NBUCKET, &uo->ucum));
     launch_user_ratio(tau, up.n2, n, r, s);
     launch_bucket_sort(r, n, false, hist, offs, uo->uperm, uo->ucum, s);
     const int64_t n_pad = round_up(std::max<int64_t>(n, 1), BU);
-    TRY(pack(c, ps, U, n, ldu, d, uo->uperm, n_pad, bpack, &uo->pack, s));
-    TRY(c->ensure(bnrm, n, &uo->nrm_s));
-    TRY(c->ensure(btau, n, &uo->tau_s));
-    TRY(c->ensure(btid, n, &uo->tid_s));
+    TRY(pack(c, ps, U, n, ldu, d, uo->uperm, n_pad, bb.pack, &uo->pack, s));
+    TRY(c->ensure(bb.nrm, n, &uo->nrm_s));
+    TRY(c->ensure(bb.nhat, n, &uo->nhat_s));
+    TRY(c->ensure(bb.del, n, &uo->del_s));
+    TRY(c->ensure(bb.tau, n, &uo->tau_s));
+    TRY(c->ensure(bb.tid, n, &uo->tid_s));
     launch_gather_f32(up.nrm, uo->uperm, n, uo->nrm_s, s);
+    launch_gather_f32(up.nhat, uo->uperm, n, uo->nhat_s, s);
+    launch_gather_f32(up.del, uo->uperm, n, uo->del_s, s);
     launch_gather_f64(tau, uo->uperm, n, uo->tau_s, s);
     if (tid) launch_gather_i32(tid, uo->uperm, n, uo->tid_s, s);
     return RKM_OK;
@@ -479,17 +514,21 @@ rkm_status count_stage(rkm_ctx* c, const PathShape& ps, int64_t n, const UserOrd
     a.m = it.m;
     a.dp = ps.dp;
     a.unrm_s = uo.nrm_s;
+    a.unhat_s = uo.nhat_s;
+    a.udel_s = uo.del_s;
     a.tau_s = uo.tau_s;
     a.tid_s = uo.tid_s;
     a.uperm = uo.uperm;
     a.item_id = new_items ? nullptr : it.perm;
     a.new_items = new_items;
     a.tmax = it.tmax;
+    a.thmax = it.thmax;
+    a.tdel = it.tdel;
     a.nprefix = nprefix;
     a.unit_off = unit_off;
     a.t_begin = t_begin;
     a.group = group;
-    a.coef = ps.coef;
+    a.cacc = ps.cacc;
     a.eabs = ps.eabs;
     a.counts = cnt;
     a.band = band;
@@ -627,9 +666,8 @@ rkm_status rkm_thresholds(rkm_ctx* c, const float* U, int64_t n, int64_t ldu, co
     ItemSide it;
     {
         Phase ph(c, s, RKM_PHASE_PREP);
-        TRY(prep_rows(c, U, n, ldu, d, c->u_e, c->u_q, c->u_n2, c->u_nrm, &up, s));
-        TRY(prep_items(c, ps, P, m, ldp, d, c->p_e, c->p_q, c->p_n2, c->p_nrm, c->p_perm, c->p_nrm_s,
-                       c->p_pack, c->tmax, &it, s));
+        TRY(prep_rows(c, ps, U, n, ldu, d, c->u_e, c->u_q, c->u_n2, c->u_nrm, c->u_nhat, c->u_del, &up, s));
+        TRY(prep_items(c, ps, P, m, ldp, d, catalogue_bufs(c), &it, s));
     }
     TRY(thresholds_core(c, ps, U, n, ldu, P, ldp, d, k, up, it, tau, tid, topk, s));
     c->stats.pairs_total = (uint64_t)n * (uint64_t)m;
@@ -644,8 +682,10 @@ static rkm_status scores_impl(rkm_ctx* c, const PathShape& ps, const float* U, i
     UserOrder uo;
     {
         Phase ph(c, s, RKM_PHASE_BOUNDS);
-        TRY(order_users(c, ps, U, n, ldu, d, up, tau, tid, c->uperm, c->ucum, c->us_pack, c->us_nrm, c->us_tau,
-                        c->us_tid, &uo, s));
+        TRY(order_users(c, ps, U, n, ldu, d, up, tau, tid,
+                        UserBufs{c->uperm, c->ucum, c->us_pack, c->us_nrm, c->us_nhat, c->us_del, c->us_tau,
+                                 c->us_tid},
+                        &uo, s));
     }
     ExactData x{U, ldu, up.e, up.q, P, ldp, it.rp.e, it.rp.q, d, (int)round_up(d, 8), &c->st->grid_u};
     int* cnt;
@@ -727,9 +767,8 @@ rkm_status rkm_scores(rkm_ctx* c, const float* U, int64_t n, int64_t ldu, const 
     ItemSide it;
     {
         Phase ph(c, s, RKM_PHASE_PREP);
-        TRY(prep_rows(c, U, n, ldu, d, c->u_e, c->u_q, c->u_n2, c->u_nrm, &up, s));
-        TRY(prep_items(c, ps, P, m, ldp, d, c->p_e, c->p_q, c->p_n2, c->p_nrm, c->p_perm, c->p_nrm_s,
-                       c->p_pack, c->tmax, &it, s));
+        TRY(prep_rows(c, ps, U, n, ldu, d, c->u_e, c->u_q, c->u_n2, c->u_nrm, c->u_nhat, c->u_del, &up, s));
+        TRY(prep_items(c, ps, P, m, ldp, d, catalogue_bufs(c), &it, s));
     }
     TRY(scores_impl(c, ps, U, n, ldu, P, ldp, d, up, it, tau, tid, 0, scores, nullptr, nullptr, false, s));
     c->stats.pairs_total = (uint64_t)n * (uint64_t)m;
@@ -771,9 +810,8 @@ rkm_status rkm_topn(rkm_ctx* c, const float* U, int64_t n, int64_t ldu, const fl
     ItemSide it;
     {
         Phase ph(c, s, RKM_PHASE_PREP);
-        TRY(prep_rows(c, U, n, ldu, d, c->u_e, c->u_q, c->u_n2, c->u_nrm, &up, s));
-        TRY(prep_items(c, ps, P, m, ldp, d, c->p_e, c->p_q, c->p_n2, c->p_nrm, c->p_perm, c->p_nrm_s,
-                       c->p_pack, c->tmax, &it, s));
+        TRY(prep_rows(c, ps, U, n, ldu, d, c->u_e, c->u_q, c->u_n2, c->u_nrm, c->u_nhat, c->u_del, &up, s));
+        TRY(prep_items(c, ps, P, m, ldp, d, catalogue_bufs(c), &it, s));
     }
     TRY(thresholds_core(c, ps, U, n, ldu, P, ldp, d, k, up, it, tau, tid, nullptr, s));
     const uint64_t cands = c->stats.candidates;
@@ -821,8 +859,9 @@ rkm_status rkm_item_bounds(rkm_ctx* c, const float* U, int64_t n, int64_t ldu, c
     if (m == 0) return RKM_OK;
     TRY(begin_call(c, s));
     RowPrep up, pp;
-    TRY(prep_rows(c, U, n, ldu, d, c->u_e, c->u_q, c->u_n2, c->u_nrm, &up, s));
-    TRY(prep_rows(c, P, m, ldp, d, c->p_e, c->p_q, c->p_n2, c->p_nrm, &pp, s));
+    const PathShape ps = path_shape(c->opts.precision, d);
+    TRY(prep_rows(c, ps, U, n, ldu, d, c->u_e, c->u_q, c->u_n2, c->u_nrm, c->u_nhat, c->u_del, &up, s));
+    TRY(prep_rows(c, ps, P, m, ldp, d, c->p_e, c->p_q, c->p_n2, c->p_nrm, c->p_nhat, c->p_del, &pp, s));
     float* r;
     unsigned *hist, *offs, *ucum;
     int* uperm;
@@ -860,10 +899,12 @@ rkm_status rkm_resident_set(rkm_ctx* c, const float* U, int64_t n, int64_t ldu, 
         CUDA_TRY(cudaMemcpyAsync(tid_c, tid, n * sizeof(int), cudaMemcpyDeviceToDevice, s));
     }
     RowPrep up;
-    TRY(prep_rows(c, Uc, n, d, d, c->res_e, c->res_q, c->u_n2, c->u_nrm, &up, s));
+    TRY(prep_rows(c, ps, Uc, n, d, d, c->res_e, c->res_q, c->u_n2, c->u_nrm, c->u_nhat, c->u_del, &up, s));
     UserOrder uo;
-    TRY(order_users(c, ps, Uc, n, d, d, up, tau_c, tid_c, c->res_uperm, c->res_ucum, c->res_pack, c->res_nrm_s,
-                    c->res_tau_s, c->res_tid_s, &uo, s));
+    TRY(order_users(c, ps, Uc, n, d, d, up, tau_c, tid_c,
+                    UserBufs{c->res_uperm, c->res_ucum, c->res_pack, c->res_nrm_s, c->res_nhat_s, c->res_del_s,
+                             c->res_tau_s, c->res_tid_s},
+                    &uo, s));
     TRY(read_status(c, s));
     c->res_grid = c->st_host->grid_u;
     c->res_n = n;
@@ -896,12 +937,12 @@ rkm_status rkm_query_new_items(rkm_ctx* c, const float* Q, int64_t q, int64_t ld
     ItemSide it;
     {
         Phase ph(c, s, RKM_PHASE_PREP);
-        TRY(prep_items(c, ps, Q, q, ldq, d, c->q_e, c->q_q, c->q_n2, c->q_nrm, c->q_perm, c->q_nrm_s,
-                       c->q_pack, c->q_tmax, &it, s));
+        TRY(prep_items(c, ps, Q, q, ldq, d, query_bufs(c), &it, s));
     }
-    UserOrder uo{static_cast<int*>(c->res_uperm.p), static_cast<unsigned*>(c->res_ucum.p), c->res_pack.p,
-                 static_cast<float*>(c->res_nrm_s.p), static_cast<double*>(c->res_tau_s.p),
-                 static_cast<int*>(c->res_tid_s.p)};
+    UserOrder uo{static_cast<int*>(c->res_uperm.p),    static_cast<unsigned*>(c->res_ucum.p),
+                 c->res_pack.p,                          static_cast<float*>(c->res_nrm_s.p),
+                 static_cast<float*>(c->res_nhat_s.p),   static_cast<float*>(c->res_del_s.p),
+                 static_cast<double*>(c->res_tau_s.p),   static_cast<int*>(c->res_tid_s.p)};
     ExactData x{static_cast<const float*>(c->res_U.p), d, static_cast<const int*>(c->res_e.p),
                 static_cast<const int16_t*>(c->res_q.p), Q, ldq, it.rp.e, it.rp.q, d, (int)round_up(d, 8),
                 &c->st->grid_u};

@@ -75,9 +75,22 @@ __device__ __forceinline__ T warp_sum(T v) {
     return v;
 }
 
-// Error bound of one approximate product, E = coef * ||u|| * ||p||max + eabs, rounded up.
-__device__ __forceinline__ float err_bound(float coef, float eabs, float un, float pn) {
-    return __fadd_ru(__fmul_ru(coef, __fmul_ru(un, pn)), eabs);
+// Error bound of one approximate product v of u^ . p^ (operands u^, p^ rounded from u, p):
+//   |v - u.p| <= |u^.p^ - u.p| + |v - u^.p^|
+//             <= ||u^ - u|| ||p^|| + ||u|| ||p^ - p|| + cacc ||u^|| ||p^|| + eabs
+// by Cauchy-Schwarz on (u^ - u).p^ + u.(p^ - p), with the tile maxima of the item
+// terms; every operation rounds up.
+__device__ __forceinline__ float err_bound(float cacc, float eabs, float un, float unhat, float udel,
+                                           float pnhat, float pdel) {
+    const float rep = __fadd_ru(__fmul_ru(udel, pnhat), __fmul_ru(un, pdel));
+    return __fadd_ru(__fadd_ru(rep, __fmul_ru(cacc, __fmul_ru(unhat, pnhat))), eabs);
+}
+
+// Three-input maximum (sm_100 and later).
+__device__ __forceinline__ float fmax3f(float a, float b, float c) {
+    float d;
+    asm("max.f32 %0, %1, %2, %3;" : "=f"(d) : "f"(a), "f"(b), "f"(c));
+    return d;
 }
 
 }  // namespace rkm

@@ -49,16 +49,31 @@ static __device__ __noinline__ int compact_candidates(Cand* c, int cnt, float L)
 }
 
 struct SelState {
-    float L;    // root of the lower-bound heap (k-th largest v - E so far)
-    float thr;  // L - E of the current tile, rounded down
-    int cnt;    // candidates stored
+    float L;     // root of the lower-bound heap (k-th largest v - E so far)
+    float Lx;    // a lower bound of tau_u published by the other epilogue group (or -inf)
+    float thr;   // max(L, Lx) - E of the current tile, rounded down
+    int cnt;     // candidates stored
+    unsigned long long* pub;  // where this group publishes L for the other group (null: none)
+    unsigned tag;             // user tile the published bound belongs to
 };
 
+// A published bound: (user tile << 32) | bits of L, written and read as one 64-bit word so a
+// reader never mixes a bound with the tag of another user tile.
+__device__ __forceinline__ void publish_bound(unsigned long long* p, unsigned tag, float L) {
+    *reinterpret_cast<volatile unsigned long long*>(p) =
+        ((unsigned long long)tag << 32) | (unsigned long long)__float_as_uint(L);
+}
+
+__device__ __forceinline__ float read_bound(const unsigned long long* p, unsigned tag) {
+    const unsigned long long x = *reinterpret_cast<const volatile unsigned long long*>(p);
+    return ((unsigned)(x >> 32) == tag) ? __uint_as_float((unsigned)(x & 0xffffffffull)) : -INFINITY;
+}
+
 __device__ __forceinline__ void sel_insert(float v, int pos, float E, SelState& s, Cand* mycand, int cap,
-                                        float* heap, int t, int k, DevStatus* st) {
+                                           float* heap, int t, int k, DevStatus* st) {
     const float ub = __fadd_ru(v, E);
     const float lb = __fsub_rd(v, E);
-    if (s.cnt >= cap) s.cnt = compact_candidates(mycand, s.cnt, s.L);
+    if (s.cnt >= cap) s.cnt = compact_candidates(mycand, s.cnt, fmaxf(s.L, s.Lx));
     if (s.cnt < cap) {
         Cand c;
         c.ub = ub;
@@ -70,31 +85,66 @@ __device__ __forceinline__ void sel_insert(float v, int pos, float E, SelState& 
     if (lb > s.L) {
         heap_replace_root(heap, t, k, lb);
         s.L = heap[t];
-        s.thr = __fsub_rd(s.L, E);
+        if (s.pub) publish_bound(s.pub, s.tag, s.L);
+        s.thr = __fsub_rd(fmaxf(s.L, s.Lx), E);
     }
 }
 
-__device__ __forceinline__ float max32(const float (&v)[32]) {
-    float a = fmaxf(v[0], v[1]), b = fmaxf(v[2], v[3]);
+// x = v[c] for a run-time c in [0, 32): a five-level select tree (no local memory).
+__device__ __forceinline__ float select32(const float (&v)[32], int c) {
+    float l1[16], l2[8], l3[4], l4[2];
 #pragma unroll
-    for (int c = 4; c < 32; c += 4) {
-        a = fmaxf(a, fmaxf(v[c], v[c + 1]));
-        b = fmaxf(b, fmaxf(v[c + 2], v[c + 3]));
-    }
-    return fmaxf(a, b);
+    for (int i = 0; i < 16; ++i) l1[i] = (c & 1) ? v[2 * i + 1] : v[2 * i];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) l2[i] = (c & 2) ? l1[2 * i + 1] : l1[2 * i];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) l3[i] = (c & 4) ? l2[2 * i + 1] : l2[2 * i];
+#pragma unroll
+    for (int i = 0; i < 2; ++i) l4[i] = (c & 8) ? l3[2 * i + 1] : l3[2 * i];
+    return (c & 16) ? l4[1] : l4[0];
 }
 
-// Threshold-pass epilogue of one 32-column chunk.  Must be called by all 32 lanes of
-// the warp (warp-uniform fast path); `active` masks lanes without a valid user.
+// Maxima of the four 8-column groups of a chunk.
+__device__ __forceinline__ void group_max8(const float (&v)[32], float (&g)[4]) {
+#pragma unroll
+    for (int q = 0; q < 4; ++q)
+        g[q] = fmax3f(fmax3f(v[8 * q], v[8 * q + 1], v[8 * q + 2]), fmax3f(v[8 * q + 3], v[8 * q + 4], v[8 * q + 5]),
+                      fmaxf(v[8 * q + 6], v[8 * q + 7]));
+}
+
+// Bit c of the result is set when v[c] >= thr, for the 8-column groups whose maximum g[q]
+// reaches thr in some lane of the warp (all 32 lanes must call it).
+__device__ __forceinline__ unsigned hit_mask(const float (&v)[32], const float (&g)[4], bool active, float thr) {
+    unsigned mask = 0u;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        const bool hq = active && g[q] >= thr;
+        if (__any_sync(0xffffffffu, hq) && hq) {
+#pragma unroll
+            for (int j = 0; j < 8; ++j) mask |= (v[8 * q + j] >= thr ? 1u : 0u) << (8 * q + j);
+        }
+    }
+    return mask;
+}
+
+// Threshold-pass epilogue of one 32-column chunk.  Must be called by all 32 lanes of the
+// warp: the fast path is one maximum tree and one vote; 8-column groups in which some lane
+// reaches its threshold are compared element by element, and the hits are inserted one by
+// one through a single call site.  `active` masks lanes without a valid user.
 __device__ __forceinline__ void sel_chunk(const float (&v)[32], bool active, int pos0, int64_t m,
                                           float E, SelState& s, Cand* mycand, int cap, float* heap,
                                           int t, int k, DevStatus* st) {
-    const bool hit = active && (max32(v) >= s.thr);
-    if (!__any_sync(0xffffffffu, hit)) return;
-    if (hit) {
-#pragma unroll
-        for (int c = 0; c < 32; ++c)
-            if (v[c] >= s.thr && pos0 + c < m) sel_insert(v[c], pos0 + c, E, s, mycand, cap, heap, t, k, st);
+    float g[4];
+    group_max8(v, g);
+    const float mx = fmax3f(g[0], g[1], fmaxf(g[2], g[3]));
+    if (!__any_sync(0xffffffffu, active && mx >= s.thr)) return;
+    unsigned mask = hit_mask(v, g, active, s.thr);
+    while (mask) {
+        const int c = __ffs(mask) - 1;
+        mask &= mask - 1u;
+        const float x = select32(v, c);
+        // s.thr only grows, so skipping values now below it is still sound.
+        if (x >= s.thr && pos0 + c < m) sel_insert(x, pos0 + c, E, s, mycand, cap, heap, t, k, st);
     }
 }
 
@@ -104,21 +154,22 @@ __device__ __forceinline__ void count_chunk(const float (&v)[32], bool active, i
                                             int64_t mlim, float hi, float lo, int* cnt_s,
                                             int u_orig, int2* band, unsigned band_cap,
                                             DevStatus* st) {
-    const bool hit = active && (max32(v) >= lo);
-    if (!__any_sync(0xffffffffu, hit)) return;
-    if (hit) {
-#pragma unroll
-        for (int c = 0; c < 32; ++c) {
-            const float x = v[c];
-            if (x >= lo && pos0 + c < mlim) {
-                if (x > hi) {
-                    atomicAdd(&cnt_s[col0 + c], 1);
-                } else {
-                    unsigned idx = atomicAdd(&st->band_count, 1u);
-                    if (idx < band_cap) band[idx] = make_int2(u_orig, pos0 + c);
-                    else st->band_overflow = 1u;
-                }
-            }
+    float g[4];
+    group_max8(v, g);
+    const float mx = fmax3f(g[0], g[1], fmaxf(g[2], g[3]));
+    if (!__any_sync(0xffffffffu, active && mx >= lo)) return;
+    unsigned mask = hit_mask(v, g, active, lo);
+    while (mask) {
+        const int c = __ffs(mask) - 1;
+        mask &= mask - 1u;
+        if (pos0 + c >= mlim) continue;
+        const float x = select32(v, c);
+        if (x > hi) {
+            atomicAdd(&cnt_s[col0 + c], 1);
+        } else {
+            unsigned idx = atomicAdd(&st->band_count, 1u);
+            if (idx < band_cap) band[idx] = make_int2(u_orig, pos0 + c);
+            else st->band_overflow = 1u;
         }
     }
 }

@@ -18,8 +18,11 @@ inline void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); 
 
 // Per row: exponent e (max|x| <= 2^e), integer grid codes q = x * 2^(12-e) (int16,
 // row stride dq), exact/upper-bound squared norm, ||x|| rounded up, grid flag.
+// Also ||x^|| and ||x^ - x|| (rounded up) of the operand x^ the product kernels see:
+// x^ = BF16 round-to-nearest of x when round_bf16, else x itself.
 void launch_prep_rows(const float* X, int64_t rows, int64_t ld, int d, int* ex, int16_t* q,
-                      int dq, double* norm2, float* nrm_hi, unsigned* grid_flag, cudaStream_t s);
+                      int dq, double* norm2, float* nrm_hi, float* nhat_hi, float* del_hi,
+                      bool round_bf16, unsigned* grid_flag, cudaStream_t s);
 
 // Zero-padded operand copy dst[r][c] (rows_pad x dp) of X (row perm[r] if perm != null).
 void launch_pack_f32(const float* X, int64_t rows, int64_t ld, int d, const int* perm,
@@ -38,9 +41,10 @@ void launch_gather_f32(const float* src, const int* perm, int64_t count, float* 
 void launch_gather_f64(const double* src, const int* perm, int64_t count, double* dst, cudaStream_t s);
 void launch_gather_i32(const int* src, const int* perm, int64_t count, int* dst, cudaStream_t s);
 
-// Maximum of vals[t*tile .. min(count,(t+1)*tile)) per tile (0 for an empty tile).
-void launch_tile_max(const float* vals, int64_t count, int tile, int64_t tiles, float* out,
-                     cudaStream_t s);
+// Per tile t of sorted positions [t*tile, min(count,(t+1)*tile)): the maxima of nrm, nhat and
+// del over the rows perm[pos] (0 for an empty tile).
+void launch_tile_max(const float* nrm, const float* nhat, const float* del, const int* perm, int64_t count,
+                     int tile, int64_t tiles, float* tmax, float* thmax, float* tdel, cudaStream_t s);
 
 // K4: r_u = tau_u / ||u|| rounded down (-inf when tau_u <= 0).
 void launch_user_ratio(const double* tau, const double* norm2, int64_t n, float* r, cudaStream_t s);
@@ -57,8 +61,12 @@ struct ThresholdArgs {
     int64_t n, m;
     int dp, k, cap;
     const float* unrm;    // [n] ||u|| rounded up
+    const float* unhat;   // [n] ||u^|| rounded up (u^ = operand seen by the product)
+    const float* udel;    // [n] ||u^ - u|| rounded up
     const float* tmax;    // [item tiles] max ||p|| of the tile, rounded up
-    float coef, eabs;     // error bound E = coef*||u||*tmax + eabs
+    const float* thmax;   // [item tiles] max ||p^||
+    const float* tdel;    // [item tiles] max ||p^ - p||
+    float cacc, eabs;     // accumulation coefficient and absolute (underflow) term of the bound
     Cand* cand;           // [n][nseg][cap]
     int* cand_cnt;        // [n][nseg]
     unsigned* lfin_key;   // [n] float_key of the final lower threshold L_u (atomic max; 0 = none)
@@ -105,17 +113,21 @@ struct CountArgs {
     int64_t n, m;
     int dp;
     const float* unrm_s;    // [n] ||u|| rounded up, ratio order
+    const float* unhat_s;   // [n] ||u^||, ratio order
+    const float* udel_s;    // [n] ||u^ - u||, ratio order
     const double* tau_s;    // [n] ratio order
     const int* tid_s;       // [n] ratio order (ignored for new items)
     const int* uperm;       // ratio order -> original user id
     const int* item_id;     // sorted pos -> original item id (null for new items)
     bool new_items;         // strict rule u.p > tau_u (new ids beat no tie)
-    const float* tmax;      // per item tile
+    const float* tmax;      // per item tile: max ||p||
+    const float* thmax;     // per item tile: max ||p^||
+    const float* tdel;      // per item tile: max ||p^ - p||
     const int* nprefix;     // per item tile: users needed (ratio-order prefix length)
     const unsigned* unit_off;  // [tiles+1] work units per item tile, exclusive scan
     int t_begin;            // first item tile of the stage
     int group;              // user tiles per work unit
-    float coef, eabs;
+    float cacc, eabs;
     int* counts;            // [m] by sorted position
     int2* band; unsigned band_cap;
     DevStatus* st;

@@ -26,6 +26,7 @@ inline int grid_for(int64_t work, int per_block, int cap = 1 << 20) {
 __global__ void k_prep_rows(const float* __restrict__ X, int64_t rows, int64_t ld, int d,
                             int* __restrict__ ex, int16_t* __restrict__ q, int dq,
                             double* __restrict__ norm2, float* __restrict__ nrm_hi,
+                            float* __restrict__ nhat_hi, float* __restrict__ del_hi, int round_bf16,
                             unsigned* grid_flag) {
     const int lane = threadIdx.x & 31;
     const int64_t warps = ((int64_t)gridDim.x * blockDim.x) >> 5;
@@ -42,7 +43,7 @@ __global__ void k_prep_rows(const float* __restrict__ X, int64_t rows, int64_t l
         }
         bool ok = true;
         long long s2 = 0;
-        double d2 = 0.0;
+        double d2 = 0.0, h2 = 0.0, e2 = 0.0;
         for (int j = lane; j < dq; j += 32) {
             float v = (j < d) ? x[j] : 0.f;
             float t = ldexpf(v, 12 - e);
@@ -52,10 +53,17 @@ __global__ void k_prep_rows(const float* __restrict__ X, int64_t rows, int64_t l
             q[row * dq + j] = (int16_t)qi;
             s2 += (long long)qi * qi;
             d2 = fma((double)v, (double)v, d2);
+            // Operand the product kernels see, and its rounding error (exact in FP32).
+            const float vh = round_bf16 ? __bfloat162float(__float2bfloat16_rn(v)) : v;
+            const float dv = vh - v;
+            h2 = fma((double)vh, (double)vh, h2);
+            e2 = fma((double)dv, (double)dv, e2);
         }
         ok = __all_sync(0xffffffffu, ok);
         s2 = warp_sum(s2);
         d2 = warp_sum(d2);
+        h2 = warp_sum(h2);
+        e2 = warp_sum(e2);
         if (lane == 0) {
             double n2;
             if (ok) {
@@ -68,6 +76,9 @@ __global__ void k_prep_rows(const float* __restrict__ X, int64_t rows, int64_t l
             ex[row] = e;
             norm2[row] = n2;
             nrm_hi[row] = __double2float_ru(__dsqrt_ru(n2));
+            // FP64 sums of at most 256 exact squares: widen by 2^-40 to bound the rounding.
+            nhat_hi[row] = __double2float_ru(__dsqrt_ru(h2 * (1.0 + 0x1p-40)));
+            del_hi[row] = __double2float_ru(__dsqrt_ru(e2 * (1.0 + 0x1p-40)));
         }
     }
 }
@@ -154,17 +165,31 @@ __global__ void k_gather(const T* __restrict__ src, const int* __restrict__ perm
         dst[i] = src[perm[i]];
 }
 
-__global__ void k_tile_max(const float* __restrict__ vals, int64_t count, int tile, int64_t tiles,
-                           float* __restrict__ out) {
+// Per tile of `tile` consecutive sorted rows: max ||p||, max ||p^||, max ||p^ - p||.
+__global__ void k_tile_max(const float* __restrict__ nrm, const float* __restrict__ nhat,
+                           const float* __restrict__ del, const int* __restrict__ perm, int64_t count, int tile,
+                           int64_t tiles, float* __restrict__ tmax, float* __restrict__ thmax,
+                           float* __restrict__ tdel) {
     const int lane = threadIdx.x & 31;
     const int64_t warps = ((int64_t)gridDim.x * blockDim.x) >> 5;
     for (int64_t t = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; t < tiles; t += warps) {
-        float mx = 0.f;
-        int64_t b = t * tile, e = b + tile;
-        if (e > count) e = count;
-        for (int64_t i = b + lane; i < e; i += 32) mx = fmaxf(mx, vals[i]);
-        mx = warp_max(mx);
-        if (lane == 0) out[t] = mx;
+        float a = 0.f, b = 0.f, c = 0.f;
+        int64_t i0 = t * tile, i1 = i0 + tile;
+        if (i1 > count) i1 = count;
+        for (int64_t i = i0 + lane; i < i1; i += 32) {
+            const int src = perm[i];
+            a = fmaxf(a, nrm[src]);
+            b = fmaxf(b, nhat[src]);
+            c = fmaxf(c, del[src]);
+        }
+        a = warp_max(a);
+        b = warp_max(b);
+        c = warp_max(c);
+        if (lane == 0) {
+            tmax[t] = a;
+            thmax[t] = b;
+            tdel[t] = c;
+        }
     }
 }
 
@@ -194,11 +219,13 @@ __global__ void k_item_uscore(const float* __restrict__ nrm_hi, int64_t m,
 }  // namespace
 
 void launch_prep_rows(const float* X, int64_t rows, int64_t ld, int d, int* ex, int16_t* q, int dq,
-                      double* norm2, float* nrm_hi, unsigned* grid_flag, cudaStream_t s) {
+                      double* norm2, float* nrm_hi, float* nhat_hi, float* del_hi, bool round_bf16,
+                      unsigned* grid_flag, cudaStream_t s) {
     if (rows <= 0) return;
     note_launch();
     k_prep_rows<<<grid_for(rows * 32, 256, 65536), 256, 0, s>>>(X, rows, ld, d, ex, q, dq, norm2,
-                                                                 nrm_hi, grid_flag);
+                                                                 nrm_hi, nhat_hi, del_hi, round_bf16 ? 1 : 0,
+                                                                 grid_flag);
 }
 
 void launch_pack_f32(const float* X, int64_t rows, int64_t ld, int d, const int* perm, float* dst,
@@ -251,11 +278,12 @@ void launch_gather_i32(const int* src, const int* perm, int64_t count, int* dst,
     }
 }
 
-void launch_tile_max(const float* vals, int64_t count, int tile, int64_t tiles, float* out,
-                     cudaStream_t s) {
+void launch_tile_max(const float* nrm, const float* nhat, const float* del, const int* perm, int64_t count,
+                     int tile, int64_t tiles, float* tmax, float* thmax, float* tdel, cudaStream_t s) {
     if (tiles > 0) {
         note_launch();
-        k_tile_max<<<grid_for(tiles * 32, 256, 65536), 256, 0, s>>>(vals, count, tile, tiles, out);
+        k_tile_max<<<grid_for(tiles * 32, 256, 65536), 256, 0, s>>>(nrm, nhat, del, perm, count, tile, tiles,
+                                                                     tmax, thmax, tdel);
     }
 }
 

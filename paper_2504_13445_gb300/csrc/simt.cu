@@ -108,22 +108,27 @@ __global__ void __launch_bounds__(SIMT_THREADS, 1) k_threshold_simt(ThresholdArg
         const bool active = owner && u < a.n;
         SelState s;
         s.L = -INFINITY;
+        s.Lx = -INFINITY;
         s.thr = -INFINITY;
         s.cnt = 0;
-        float un = 0.f;
+        s.pub = nullptr;
+        s.tag = 0u;
+        float un = 0.f, unh = 0.f, ud = 0.f;
         Cand* mycand = nullptr;
         if (owner) {
             for (int j = 0; j < a.k; ++j) heap[j * BU + t] = -INFINITY;
             if (active) {
                 un = a.unrm[u];
+                unh = a.unhat[u];
+                ud = a.udel[u];
                 mycand = a.cand + u * (int64_t)a.nseg * a.cap;
             }
         }
         for (int64_t it = 0; it < item_tiles; ++it) {
             simt_tile(A, ut * BU, B, it * BI_SIMT, a.dp, sm);
             if (owner) {
-                const float E = err_bound(a.coef, a.eabs, un, a.tmax[it]);
-                s.thr = __fsub_rd(s.L, E);
+                const float E = err_bound(a.cacc, a.eabs, un, unh, ud, a.thmax[it], a.tdel[it]);
+                s.thr = __fsub_rd(fmaxf(s.L, s.Lx), E);
 #pragma unroll 1
                 for (int c0 = 0; c0 < BI_SIMT; c0 += 32) {
                     float v[32];
@@ -172,7 +177,7 @@ __global__ void __launch_bounds__(SIMT_THREADS, 1) k_count_simt(CountArgs a) {
         if (ut1 > ut_end_all) ut1 = ut_end_all;
         if (t < BI_SIMT) cnt_s[t] = 0;
         __syncthreads();
-        const float pn = a.tmax[T];
+        const float pnh = a.thmax[T], pd = a.tdel[T];
         const int pos0 = T * BI_SIMT;
         for (int64_t ut = ut0; ut < ut1; ++ut) {
             simt_tile(A, ut * BU, B, (int64_t)T * BI_SIMT, a.dp, sm);
@@ -182,7 +187,7 @@ __global__ void __launch_bounds__(SIMT_THREADS, 1) k_count_simt(CountArgs a) {
                 float hi_t = 0.f, lo_t = 0.f;
                 int u_orig = 0;
                 if (active) {
-                    const float E = err_bound(a.coef, a.eabs, a.unrm_s[us], pn);
+                    const float E = err_bound(a.cacc, a.eabs, a.unrm_s[us], a.unhat_s[us], a.udel_s[us], pnh, pd);
                     const double tau = a.tau_s[us];
                     hi_t = __fadd_ru(__double2float_ru(tau), E);
                     lo_t = __fsub_rd(__double2float_rd(tau), E);

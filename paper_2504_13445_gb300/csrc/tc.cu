@@ -118,6 +118,11 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     const int64_t user_tiles = (a.n + BU - 1) / BU;
     const int64_t item_tiles = (a.m + BI_TC - 1) / BI_TC;
     volatile int* abort = &B->abort;
+    // Running bounds published per user row by each epilogue group: Lpub[h][row], tagged with
+    // the user tile (a bound of another user tile is never used).  Initialised before setup's
+    // barrier so that no group can read an uninitialised entry.
+    unsigned long long* Lpub = reinterpret_cast<unsigned long long*>(heaps + 2 * a.k * BU);
+    if (warp >= 2) Lpub[threadIdx.x - 64] = 0xFFFFFFFF00000000ull;
 
     setup(B, S, warp);
     const uint32_t tmem = B->tmem_base;
@@ -217,9 +222,14 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             for (int j = 0; j < a.k; ++j) heap[j * BU + r] = -INFINITY;
             SelState s;
             s.L = -INFINITY;
+            s.Lx = -INFINITY;
             s.thr = -INFINITY;
             s.cnt = 0;
+            s.pub = &Lpub[h * BU + r];
+            s.tag = (unsigned)ut;
             const float un = active ? a.unrm[u] : 0.f;
+            const float unh = active ? a.unhat[u] : 0.f;
+            const float ud = active ? a.udel[u] : 0.f;
             Cand* mycand = a.cand + ((active ? u : 0) * a.nseg + h) * (int64_t)a.cap;
             for (int64_t it = 0; it < item_tiles; ++it) {
                 const uint32_t b = tile_j & 1u, use = tile_j >> 1;
@@ -231,15 +241,37 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                 }
                 __syncwarp();
                 tc_fence_after();
-                const float E = err_bound(a.coef, a.eabs, un, a.tmax[it]);
-                s.thr = __fsub_rd(s.L, E);
+                const float E = err_bound(a.cacc, a.eabs, un, unh, ud, a.thmax[it], a.tdel[it]);
+                // The partner's bound may be stale or from this user tile's start (-inf):
+                // any value it held is a valid lower bound of tau_u for the current user.
+                s.Lx = read_bound(&Lpub[(1 - h) * BU + r], (unsigned)ut);
+                s.thr = __fsub_rd(fmaxf(s.L, s.Lx), E);
                 const uint32_t tb = tmem + ((uint32_t)(q * 32) << 16) + b * BI_TC;
+                // Two register buffers: the load of the next 32 columns overlaps the current chunk.
+                uint32_t ra[32], rb[32];
+                tmem_ld32_issue(tb, ra);
+                tmem_wait_bind(ra);
 #pragma unroll 1
-                for (int c0 = 0; c0 < BI_TC; c0 += 32) {
-                    float v[32];
+                for (int c0 = 0; c0 < BI_TC; c0 += 64) {
                     __syncwarp();
-                    tmem_ld32(tb + c0, v);
-                    sel_chunk(v, active, (int)(it * BI_TC + c0), a.m, E, s, mycand, a.cap, heap, r, a.k, a.st);
+                    tmem_ld32_issue(tb + c0 + 32, rb);
+                    {
+                        float v[32];
+                        as_floats(ra, v);
+                        sel_chunk(v, active, (int)(it * BI_TC + c0), a.m, E, s, mycand, a.cap, heap, r, a.k,
+                                  a.st);
+                    }
+                    __syncwarp();
+                    tmem_wait_bind(rb);
+                    if (c0 + 64 < BI_TC) tmem_ld32_issue(tb + c0 + 64, ra);
+                    {
+                        float v[32];
+                        as_floats(rb, v);
+                        sel_chunk(v, active, (int)(it * BI_TC + c0 + 32), a.m, E, s, mycand, a.cap, heap, r,
+                                  a.k, a.st);
+                    }
+                    __syncwarp();
+                    if (c0 + 64 < BI_TC) tmem_wait_bind(ra);
                 }
                 tc_fence_before();
                 __syncwarp();
@@ -395,7 +427,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             int T;
             int64_t ut0, ut1;
             decode_unit(a, w, len, T, ut0, ut1);
-            const float pn = a.tmax[T];
+            const float pnh = a.thmax[T], pd = a.tdel[T];
             const int pos0 = T * BI_TC;
             for (int64_t ut = ut0; ut < ut1; ++ut) {
                 const uint32_t b = tile_j & 1u, use = tile_j >> 1;
@@ -412,19 +444,38 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                 float hi_t = 0.f, lo_t = 0.f;
                 int u_orig = 0;
                 if (active) {
-                    const float E = err_bound(a.coef, a.eabs, a.unrm_s[us], pn);
+                    const float E =
+                        err_bound(a.cacc, a.eabs, a.unrm_s[us], a.unhat_s[us], a.udel_s[us], pnh, pd);
                     const double tau = a.tau_s[us];
                     hi_t = __fadd_ru(__double2float_ru(tau), E);
                     lo_t = __fsub_rd(__double2float_rd(tau), E);
                     u_orig = a.uperm[us];
                 }
                 const uint32_t tb = tmem + ((uint32_t)(q * 32) << 16) + b * BI_TC;
+                uint32_t ra[32], rb[32];
+                tmem_ld32_issue(tb, ra);
+                tmem_wait_bind(ra);
 #pragma unroll 1
-                for (int c0 = 0; c0 < BI_TC; c0 += 32) {
-                    float v[32];
+                for (int c0 = 0; c0 < BI_TC; c0 += 64) {
                     __syncwarp();
-                    tmem_ld32(tb + c0, v);
-                    count_chunk(v, active, c0, pos0 + c0, a.m, hi_t, lo_t, cw, u_orig, a.band, a.band_cap, a.st);
+                    tmem_ld32_issue(tb + c0 + 32, rb);
+                    {
+                        float v[32];
+                        as_floats(ra, v);
+                        count_chunk(v, active, c0, pos0 + c0, a.m, hi_t, lo_t, cw, u_orig, a.band, a.band_cap,
+                                    a.st);
+                    }
+                    __syncwarp();
+                    tmem_wait_bind(rb);
+                    if (c0 + 64 < BI_TC) tmem_ld32_issue(tb + c0 + 64, ra);
+                    {
+                        float v[32];
+                        as_floats(rb, v);
+                        count_chunk(v, active, c0 + 32, pos0 + c0 + 32, a.m, hi_t, lo_t, cw, u_orig, a.band,
+                                    a.band_cap, a.st);
+                    }
+                    __syncwarp();
+                    if (c0 + 64 < BI_TC) tmem_wait_bind(ra);
                 }
                 tc_fence_before();
                 __syncwarp();
@@ -501,7 +552,7 @@ rkm_status make_tmaps(const void* A, int64_t a_rows, const void* B, int64_t b_ro
 
 void launch_threshold_tc(const ThresholdArgs& a, const void* tmapA, const void* tmapB, cudaStream_t s) {
     const int KB = a.dp / 64;
-    const TcLayout L = make_layout(KB * KB_BYTES_U, KB_BYTES_I, 2u * BU * a.k * 4u, MAX_SLOTS);
+    const TcLayout L = make_layout(KB * KB_BYTES_U, KB_BYTES_I, 2u * BU * a.k * 4u + 2u * BU * 8u, MAX_SLOTS);
     cudaFuncSetAttribute(k_threshold_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.bytes);
     const int64_t user_tiles = (a.n + BU - 1) / BU;
     const int grid = (int)(user_tiles < a.num_sms ? user_tiles : a.num_sms);
