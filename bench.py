@@ -248,7 +248,7 @@ def run_ours(args, rank, local, world):
     barrier(world)
     clocks.start()
     torch.cuda.synchronize()
-    step_ms, thr_ms, thr_launch, launches, counted, cand, band = [], [], [], 0, [], [], []
+    step_ms, thr_ms, thr_launch, launches, counted, cand, band, evald = [], [], [], 0, [], [], [], []
     for _ in range(args.steps):
         flush.zero_()
         e0 = torch.cuda.Event(enable_timing=True)
@@ -265,6 +265,7 @@ def run_ours(args, rank, local, world):
         counted.append(st["items_counted"])
         cand.append(st["candidates"])
         band.append(st["band_pairs"])
+        evald.append(st["pairs_evaluated"])
     torch.cuda.synchronize()
     clk = clocks.stop()
     barrier(world)
@@ -323,7 +324,8 @@ def run_ours(args, rank, local, world):
             "gpu_launches": int(launches),
             "clocks": clk,
             "detail": {"items_counted_mean": statistics.mean(counted), "candidates_mean": statistics.mean(cand),
-                       "band_pairs_mean": statistics.mean(band), "phase_ms_last_step": st["phase_ms"]}}
+                       "band_pairs_mean": statistics.mean(band), "pairs_evaluated_mean": statistics.mean(evald),
+                       "retries_last_step": st["retries"], "phase_ms_last_step": st["phase_ms"]}}
     if e2e:
         line["e2e"] = e2e
     if not args.no_cpu_baseline and world == 1:

@@ -81,20 +81,20 @@ struct rkm_ctx {
     // threshold pass
     Buf cand, cand_cnt, lfin, keys, kid;
     // counting pass
-    Buf r_u, uperm, ucum, us_pack, us_nrm, us_nhat, us_del, us_tau, us_tid, nprefix, unit_off, band, cnt_s,
-        top_ids, top_sc, tau_tmp, tid_tmp;
+    Buf r_u, uperm, ucum, us_pack, us_meta, nprefix, unit_off, band, cnt_s, top_ids, top_sc, tau_tmp,
+        tid_tmp;
     // serving (resident users)
     bool resident = false;
     int64_t res_n = 0;
     int res_d = 0;
     unsigned res_grid = 0;
-    Buf res_U, res_e, res_q, res_tau, res_tid, res_uperm, res_ucum, res_pack, res_nrm_s, res_nhat_s,
-        res_del_s, res_tau_s, res_tid_s;
+    Buf res_U, res_e, res_q, res_tau, res_tid, res_uperm, res_ucum, res_pack, res_meta;
     // query scratch
     Buf q_e, q_q, q_n2, q_nrm, q_nhat, q_del, q_perm, q_pack, q_tmax, q_thmax, q_tdel, q_cnt;
     // host staging for rkm_topn_host
     Buf h_U, h_P, h_ids, h_sc;
     int cand_cap = 0;
+    int cand_k = 0;
     int64_t band_cap = 0;
     // phase timing (opts.profile)
     struct Pending {
@@ -139,10 +139,10 @@ struct rkm_ctx {
     void free_all() {
         Buf* all[] = {&u_e, &u_q, &u_n2, &u_nrm, &u_nhat, &u_del, &u_pack, &p_e, &p_q, &p_n2, &p_nrm,
                       &p_nhat, &p_del, &p_perm, &p_pack, &tmax, &thmax, &tdel, &hist, &offs, &cand,
-                      &cand_cnt, &lfin, &keys, &kid, &r_u, &uperm, &ucum, &us_pack, &us_nrm, &us_nhat,
-                      &us_del, &us_tau, &us_tid, &nprefix, &unit_off, &band, &cnt_s, &top_ids, &top_sc,
+                      &cand_cnt, &lfin, &keys, &kid, &r_u, &uperm, &ucum, &us_pack, &us_meta,
+                      &nprefix, &unit_off, &band, &cnt_s, &top_ids, &top_sc,
                       &tau_tmp, &tid_tmp, &res_U, &res_e, &res_q, &res_tau, &res_tid, &res_uperm, &res_ucum,
-                      &res_pack, &res_nrm_s, &res_nhat_s, &res_del_s, &res_tau_s, &res_tid_s, &q_e, &q_q,
+                      &res_pack, &res_meta, &q_e, &q_q,
                       &q_n2, &q_nrm, &q_nhat, &q_del, &q_perm, &q_pack, &q_tmax, &q_thmax, &q_tdel, &q_cnt,
                       &h_U, &h_P, &h_ids, &h_sc};
         for (Buf* b : all) {
@@ -454,18 +454,14 @@ rkm_status thresholds_core(rkm_ctx* c, const PathShape& ps, const float* U, int6
 
 // K4 for users: ratios, bucket sort, ratio-order copies.
 struct UserOrder {
-    int* uperm;
-    unsigned* ucum;
-    void* pack;
-    float* nrm_s;
-    float* nhat_s;
-    float* del_s;
-    double* tau_s;
-    int* tid_s;
+    int* uperm;       // ratio order -> original user
+    unsigned* ucum;   // users per ratio bucket, inclusive prefix
+    void* pack;       // users packed in ratio order
+    UserMeta* meta;   // per-user records, ratio order
 };
 
 struct UserBufs {
-    Buf &perm, &cum, &pack, &nrm, &nhat, &del, &tau, &tid;
+    Buf &perm, &cum, &pack, &meta;
 };
 
 rkm_status order_users(rkm_ctx* c, const PathShape& ps, const float* U, int64_t n, int64_t ldu, int d,
@@ -482,16 +478,8 @@ rkm_status order_users(rkm_ctx* c, const PathShape& ps, const float* U, int64_t 
     launch_bucket_sort(r, n, false, hist, offs, uo->uperm, uo->ucum, s);
     const int64_t n_pad = round_up(std::max<int64_t>(n, 1), BU);
     TRY(pack(c, ps, U, n, ldu, d, uo->uperm, n_pad, bb.pack, &uo->pack, s));
-    TRY(c->ensure(bb.nrm, n, &uo->nrm_s));
-    TRY(c->ensure(bb.nhat, n, &uo->nhat_s));
-    TRY(c->ensure(bb.del, n, &uo->del_s));
-    TRY(c->ensure(bb.tau, n, &uo->tau_s));
-    TRY(c->ensure(bb.tid, n, &uo->tid_s));
-    launch_gather_f32(up.nrm, uo->uperm, n, uo->nrm_s, s);
-    launch_gather_f32(up.nhat, uo->uperm, n, uo->nhat_s, s);
-    launch_gather_f32(up.del, uo->uperm, n, uo->del_s, s);
-    launch_gather_f64(tau, uo->uperm, n, uo->tau_s, s);
-    if (tid) launch_gather_i32(tid, uo->uperm, n, uo->tid_s, s);
+    TRY(c->ensure(bb.meta, n, &uo->meta));
+    launch_user_meta(tau, up.nrm, up.nhat, up.del, uo->uperm, n, uo->meta, s);
     return RKM_OK;
 }
 
@@ -503,7 +491,7 @@ rkm_status count_stage(rkm_ctx* c, const PathShape& ps, int64_t n, const UserOrd
     unsigned* unit_off;
     TRY(c->ensure(c->nprefix, std::max<int64_t>(it.tiles, 1), &nprefix));
     TRY(c->ensure(c->unit_off, it.tiles + 2, &unit_off));
-    const int group = 8;
+    const int group = 32;  // user tiles per work unit (4096 users against one item tile)
     Phase ph_count(c, s, RKM_PHASE_COUNT);
     launch_build_units(it.tmax, uo.ucum, t_begin, t_end, t_end_from_dev ? &c->st->t_end : nullptr, BU, group,
                        nprefix, unit_off, c->st, s);
@@ -513,12 +501,7 @@ rkm_status count_stage(rkm_ctx* c, const PathShape& ps, int64_t n, const UserOrd
     a.n = n;
     a.m = it.m;
     a.dp = ps.dp;
-    a.unrm_s = uo.nrm_s;
-    a.unhat_s = uo.nhat_s;
-    a.udel_s = uo.del_s;
-    a.tau_s = uo.tau_s;
-    a.tid_s = uo.tid_s;
-    a.uperm = uo.uperm;
+    a.meta = uo.meta;
     a.item_id = new_items ? nullptr : it.perm;
     a.new_items = new_items;
     a.tmax = it.tmax;
@@ -568,10 +551,16 @@ void scatter_i32(const int* src, const int* perm, int64_t count, int* dst, cudaS
 
 rkm_status ensure_band(rkm_ctx* c, int2** band) { return c->ensure(c->band, c->band_cap, band); }
 
+// Initial capacities of a call: the option (or a default sized from n and k), or the
+// capacity a previous call on this context grew to, whichever is larger.
 void init_caps(rkm_ctx* c, int64_t n, int k) {
     int cap = c->opts.cand_capacity > 0 ? c->opts.cand_capacity : (int)round_up(2 * k + 96, 32);
-    c->cand_cap = (int)round_up(cap, 32);
-    int64_t band = c->opts.band_capacity > 0 ? c->opts.band_capacity : std::max<int64_t>(1 << 20, 4 * n);
+    cap = (int)round_up(cap, 32);
+    if (c->cand_k == k) cap = std::max(cap, c->cand_cap);
+    c->cand_cap = cap;
+    c->cand_k = k;
+    int64_t band = c->opts.band_capacity > 0 ? c->opts.band_capacity : std::max<int64_t>(1 << 22, 16 * n);
+    band = std::max<int64_t>(band, c->band_cap);
     c->band_cap = std::min<int64_t>(band, (int64_t)UINT32_MAX - 1);
 }
 
@@ -683,8 +672,7 @@ static rkm_status scores_impl(rkm_ctx* c, const PathShape& ps, const float* U, i
     {
         Phase ph(c, s, RKM_PHASE_BOUNDS);
         TRY(order_users(c, ps, U, n, ldu, d, up, tau, tid,
-                        UserBufs{c->uperm, c->ucum, c->us_pack, c->us_nrm, c->us_nhat, c->us_del, c->us_tau,
-                                 c->us_tid},
+                        UserBufs{c->uperm, c->ucum, c->us_pack, c->us_meta},
                         &uo, s));
     }
     ExactData x{U, ldu, up.e, up.q, P, ldp, it.rp.e, it.rp.q, d, (int)round_up(d, 8), &c->st->grid_u};
@@ -902,8 +890,7 @@ rkm_status rkm_resident_set(rkm_ctx* c, const float* U, int64_t n, int64_t ldu, 
     TRY(prep_rows(c, ps, Uc, n, d, d, c->res_e, c->res_q, c->u_n2, c->u_nrm, c->u_nhat, c->u_del, &up, s));
     UserOrder uo;
     TRY(order_users(c, ps, Uc, n, d, d, up, tau_c, tid_c,
-                    UserBufs{c->res_uperm, c->res_ucum, c->res_pack, c->res_nrm_s, c->res_nhat_s, c->res_del_s,
-                             c->res_tau_s, c->res_tid_s},
+                    UserBufs{c->res_uperm, c->res_ucum, c->res_pack, c->res_meta},
                     &uo, s));
     TRY(read_status(c, s));
     c->res_grid = c->st_host->grid_u;
@@ -939,10 +926,8 @@ rkm_status rkm_query_new_items(rkm_ctx* c, const float* Q, int64_t q, int64_t ld
         Phase ph(c, s, RKM_PHASE_PREP);
         TRY(prep_items(c, ps, Q, q, ldq, d, query_bufs(c), &it, s));
     }
-    UserOrder uo{static_cast<int*>(c->res_uperm.p),    static_cast<unsigned*>(c->res_ucum.p),
-                 c->res_pack.p,                          static_cast<float*>(c->res_nrm_s.p),
-                 static_cast<float*>(c->res_nhat_s.p),   static_cast<float*>(c->res_del_s.p),
-                 static_cast<double*>(c->res_tau_s.p),   static_cast<int*>(c->res_tid_s.p)};
+    UserOrder uo{static_cast<int*>(c->res_uperm.p), static_cast<unsigned*>(c->res_ucum.p), c->res_pack.p,
+                 static_cast<UserMeta*>(c->res_meta.p)};
     ExactData x{static_cast<const float*>(c->res_U.p), d, static_cast<const int*>(c->res_e.p),
                 static_cast<const int16_t*>(c->res_q.p), Q, ldq, it.rp.e, it.rp.q, d, (int)round_up(d, 8),
                 &c->st->grid_u};

@@ -35,6 +35,14 @@ struct DevStatus {
     unsigned long long pad[4];
 };
 
+// Per-user data of the counting pass, one 32-byte record per user in ratio order:
+// tau_u rounded up and down to FP32, ||u||, ||u^||, ||u^ - u|| (rounded up), original id.
+struct __align__(16) UserMeta {
+    float tau_hi, tau_lo, un, unh, ud;
+    int uorig;
+    float pad0, pad1;
+};
+
 // Candidate of the threshold pass: an upper bound of u.p and the item's sorted position.
 struct Cand {
     float ub;

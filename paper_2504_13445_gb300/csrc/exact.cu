@@ -106,15 +106,25 @@ __global__ void k_exact_tau(ExactData x, const Cand* __restrict__ cand, const in
             if (lane == 0) st->internal_error = 1u;
             continue;
         }
-        for (int j = lane; j < kept; j += 32) {
-            const unsigned long long key = kk[j];
-            const int id = ki[j];
+        // Rank of each kept candidate under (score desc, id asc) = the number of candidates
+        // before it.  Candidates are visited 32 at a time and broadcast by shuffles.
+        for (int j0 = 0; j0 < kept; j0 += 32) {
+            const int j = j0 + lane;
+            const bool mine = j < kept;
+            const unsigned long long key = mine ? kk[j] : 0ull;
+            const int id = mine ? ki[j] : 0x7fffffff;
             int rank = 0;
-            for (int r = 0; r < kept; ++r) {
-                const unsigned long long k2 = kk[r];
-                rank += (k2 > key) || (k2 == key && ki[r] < id);
+            for (int r0 = 0; r0 < kept; r0 += 32) {
+                const int rn = (kept - r0 < 32) ? kept - r0 : 32;
+                const unsigned long long k2l = (r0 + lane < kept) ? kk[r0 + lane] : 0ull;
+                const int i2l = (r0 + lane < kept) ? ki[r0 + lane] : 0x7fffffff;
+                for (int r = 0; r < rn; ++r) {
+                    const unsigned long long k2 = __shfl_sync(0xffffffffu, k2l, r);
+                    const int i2 = __shfl_sync(0xffffffffu, i2l, r);
+                    rank += (k2 > key) || (k2 == key && i2 < id);
+                }
             }
-            if (rank < k) {
+            if (mine && rank < k) {
                 if (topk) topk[u * (int64_t)k + rank] = id;
                 if (rank == k - 1) {
                     tau[u] = key_to_double(key);

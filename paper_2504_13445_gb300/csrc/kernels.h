@@ -49,6 +49,10 @@ void launch_tile_max(const float* nrm, const float* nhat, const float* del, cons
 // K4: r_u = tau_u / ||u|| rounded down (-inf when tau_u <= 0).
 void launch_user_ratio(const double* tau, const double* norm2, int64_t n, float* r, cudaStream_t s);
 
+// K4: per-user records of the counting pass, in ratio order (perm: ratio order -> user).
+void launch_user_meta(const double* tau, const float* nrm, const float* nhat, const float* del, const int* perm,
+                      int64_t n, UserMeta* meta, cudaStream_t s);
+
 // K4: uscore[i] = number of users whose ratio bucket <= bucket(||p_i||) (ucum lookup).
 void launch_item_uscore(const float* nrm_hi, int64_t m, const unsigned* ucum, int* uscore,
                         cudaStream_t s);
@@ -112,12 +116,7 @@ struct CountArgs {
     const void* B;          // items packed sorted [m_pad][dp]
     int64_t n, m;
     int dp;
-    const float* unrm_s;    // [n] ||u|| rounded up, ratio order
-    const float* unhat_s;   // [n] ||u^||, ratio order
-    const float* udel_s;    // [n] ||u^ - u||, ratio order
-    const double* tau_s;    // [n] ratio order
-    const int* tid_s;       // [n] ratio order (ignored for new items)
-    const int* uperm;       // ratio order -> original user id
+    const UserMeta* meta;   // [n] per-user record, ratio order
     const int* item_id;     // sorted pos -> original item id (null for new items)
     bool new_items;         // strict rule u.p > tau_u (new ids beat no tie)
     const float* tmax;      // per item tile: max ||p||

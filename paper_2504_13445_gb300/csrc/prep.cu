@@ -43,7 +43,8 @@ __global__ void k_prep_rows(const float* __restrict__ X, int64_t rows, int64_t l
         }
         bool ok = true;
         long long s2 = 0;
-        double d2 = 0.0, h2 = 0.0, e2 = 0.0;
+        // Upper bounds of sums of squares: every FP32 operation rounds up.
+        float d2 = 0.f, h2 = 0.f, e2 = 0.f;
         for (int j = lane; j < dq; j += 32) {
             float v = (j < d) ? x[j] : 0.f;
             float t = ldexpf(v, 12 - e);
@@ -52,33 +53,34 @@ __global__ void k_prep_rows(const float* __restrict__ X, int64_t rows, int64_t l
             int qi = gi ? (int)t : 0;
             q[row * dq + j] = (int16_t)qi;
             s2 += (long long)qi * qi;
-            d2 = fma((double)v, (double)v, d2);
+            d2 = __fmaf_ru(v, v, d2);
             // Operand the product kernels see, and its rounding error (exact in FP32).
             const float vh = round_bf16 ? __bfloat162float(__float2bfloat16_rn(v)) : v;
             const float dv = vh - v;
-            h2 = fma((double)vh, (double)vh, h2);
-            e2 = fma((double)dv, (double)dv, e2);
+            h2 = __fmaf_ru(vh, vh, h2);
+            e2 = __fmaf_ru(dv, dv, e2);
         }
         ok = __all_sync(0xffffffffu, ok);
         s2 = warp_sum(s2);
-        d2 = warp_sum(d2);
-        h2 = warp_sum(h2);
-        e2 = warp_sum(e2);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            d2 = __fadd_ru(d2, __shfl_xor_sync(0xffffffffu, d2, o));
+            h2 = __fadd_ru(h2, __shfl_xor_sync(0xffffffffu, h2, o));
+            e2 = __fadd_ru(e2, __shfl_xor_sync(0xffffffffu, e2, o));
+        }
         if (lane == 0) {
             double n2;
             if (ok) {
-                n2 = ldexp((double)s2, 2 * e - 24);
+                n2 = ldexp((double)s2, 2 * e - 24);  // exact
             } else {
-                // FP64 sum of exact squares: relative error below d * 2^-53; widen by 2^-40.
-                n2 = d2 * (1.0 + 0x1p-40);
+                n2 = (double)d2;                     // an upper bound
                 atomicAnd(grid_flag, 0u);
             }
             ex[row] = e;
             norm2[row] = n2;
-            nrm_hi[row] = __double2float_ru(__dsqrt_ru(n2));
-            // FP64 sums of at most 256 exact squares: widen by 2^-40 to bound the rounding.
-            nhat_hi[row] = __double2float_ru(__dsqrt_ru(h2 * (1.0 + 0x1p-40)));
-            del_hi[row] = __double2float_ru(__dsqrt_ru(e2 * (1.0 + 0x1p-40)));
+            nrm_hi[row] = ok ? __double2float_ru(__dsqrt_ru(n2)) : __fsqrt_ru(d2);
+            nhat_hi[row] = __fsqrt_ru(h2);
+            del_hi[row] = __fsqrt_ru(e2);
         }
     }
 }
@@ -209,6 +211,25 @@ __global__ void k_user_ratio(const double* __restrict__ tau, const double* __res
     }
 }
 
+__global__ void k_user_meta(const double* __restrict__ tau, const float* __restrict__ nrm,
+                            const float* __restrict__ nhat, const float* __restrict__ del,
+                            const int* __restrict__ perm, int64_t n, UserMeta* __restrict__ meta) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const int u = perm[i];
+        const double t = tau[u];
+        UserMeta r;
+        r.tau_hi = __double2float_ru(t);
+        r.tau_lo = __double2float_rd(t);
+        r.un = nrm[u];
+        r.unh = nhat[u];
+        r.ud = del[u];
+        r.uorig = u;
+        r.pad0 = 0.f;
+        r.pad1 = 0.f;
+        meta[i] = r;
+    }
+}
+
 __global__ void k_item_uscore(const float* __restrict__ nrm_hi, int64_t m,
                               const unsigned* __restrict__ ucum, int* __restrict__ uscore) {
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m;
@@ -291,6 +312,14 @@ void launch_user_ratio(const double* tau, const double* norm2, int64_t n, float*
     if (n > 0) {
         note_launch();
         k_user_ratio<<<grid_for(n, 256, 65536), 256, 0, s>>>(tau, norm2, n, r);
+    }
+}
+
+void launch_user_meta(const double* tau, const float* nrm, const float* nhat, const float* del, const int* perm,
+                      int64_t n, UserMeta* meta, cudaStream_t s) {
+    if (n > 0) {
+        note_launch();
+        k_user_meta<<<grid_for(n, 256, 65536), 256, 0, s>>>(tau, nrm, nhat, del, perm, n, meta);
     }
 }
 

@@ -187,11 +187,11 @@ __global__ void __launch_bounds__(SIMT_THREADS, 1) k_count_simt(CountArgs a) {
                 float hi_t = 0.f, lo_t = 0.f;
                 int u_orig = 0;
                 if (active) {
-                    const float E = err_bound(a.cacc, a.eabs, a.unrm_s[us], a.unhat_s[us], a.udel_s[us], pnh, pd);
-                    const double tau = a.tau_s[us];
-                    hi_t = __fadd_ru(__double2float_ru(tau), E);
-                    lo_t = __fsub_rd(__double2float_rd(tau), E);
-                    u_orig = a.uperm[us];
+                    const UserMeta um = a.meta[us];
+                    const float E = err_bound(a.cacc, a.eabs, um.un, um.unh, um.ud, pnh, pd);
+                    hi_t = __fadd_ru(um.tau_hi, E);
+                    lo_t = __fsub_rd(um.tau_lo, E);
+                    u_orig = um.uorig;
                 }
 #pragma unroll 1
                 for (int c0 = 0; c0 < BI_SIMT; c0 += 32) {

@@ -37,7 +37,7 @@ constexpr uint32_t KB_BYTES_I = 256 * 128;  // one K-block of 256 item rows
 constexpr int SMEM_LIMIT = 232448;          // 227 KB opt-in maximum per block
 
 struct TcBars {
-    uint64_t res_full, res_empty, drain;
+    uint64_t res_full[2], res_empty[2], drain;
     uint64_t full[MAX_SLOTS], empty[MAX_SLOTS];
     uint64_t tfull[2], tempty[2];
     uint32_t tmem_base;
@@ -46,8 +46,9 @@ struct TcBars {
 
 struct TcLayout {
     uint32_t res_off, ring_off, aux_off, bar_off, bytes;
-    uint32_t slot_bytes;
-    int slots;
+    uint32_t slot_bytes, res_bytes;  // one ring slot; one resident-operand buffer
+    int slots;                       // ring slots
+    int nres;                        // resident-operand buffers (2 = next unit loads during this one)
 };
 
 __device__ __forceinline__ uint8_t* align1024(uint8_t* raw) {
@@ -68,8 +69,10 @@ __device__ __forceinline__ void drain_wait(uint64_t* bar, uint32_t parity, DevSt
 
 __device__ __forceinline__ void setup(TcBars* B, int slots, int warp) {
     if (threadIdx.x == 0) {
-        mbar_init(&B->res_full, 1);
-        mbar_init(&B->res_empty, 1);
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(&B->res_full[b], 1);
+            mbar_init(&B->res_empty[b], 1);
+        }
         mbar_init(&B->drain, 1);
         for (int s = 0; s < slots; ++s) {
             mbar_init(&B->full[s], 1);
@@ -137,10 +140,12 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             int res_loads = 0;
             bool ok = true;
             for (int64_t ut = blockIdx.x; ut < user_tiles && ok; ut += gridDim.x) {
-                if (res_loads > 0 && !mbar_wait(&B->res_empty, (res_loads - 1) & 1, abort, a.st)) break;
-                mbar_expect_tx(&B->res_full, KB * KB_BYTES_U);
+                const int rb = res_loads % L.nres, ru = res_loads / L.nres;
+                if (ru > 0 && !mbar_wait(&B->res_empty[rb], (ru - 1) & 1, abort, a.st)) break;
+                uint8_t* dst = sA + rb * L.res_bytes;
+                mbar_expect_tx(&B->res_full[rb], KB * KB_BYTES_U);
                 for (int kb = 0; kb < KB; ++kb)
-                    tma_load_2d(sA + kb * KB_BYTES_U, &tmA, &B->res_full, kb * 64, (int)(ut * BU));
+                    tma_load_2d(dst + kb * KB_BYTES_U, &tmA, &B->res_full[rb], kb * 64, (int)(ut * BU));
                 ++res_loads;
                 for (int64_t it = 0; it < item_tiles && ok; ++it) {
                     for (int kb = 0; kb < KB; ++kb) {
@@ -161,7 +166,10 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             // Copies in flight complete on their barriers; wait for them before the CTA exits.
             for (int s = 0; s < S; ++s)
                 if (issued[s] > 0) drain_wait(&B->full[s], (uint32_t)(issued[s] - 1) & 1u, a.st);
-            if (res_loads > 0) drain_wait(&B->res_full, (uint32_t)(res_loads - 1) & 1u, a.st);
+            for (int rb = 0; rb < L.nres; ++rb) {
+                const int loads = res_loads / L.nres + (rb < res_loads % L.nres ? 1 : 0);
+                if (loads > 0) drain_wait(&B->res_full[rb], (uint32_t)(loads - 1) & 1u, a.st);
+            }
         }
     } else if (warp == 1) {
         if (lane == 0) {
@@ -171,8 +179,10 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             int iter = 0;
             bool ok = true;
             for (int64_t ut = blockIdx.x; ut < user_tiles && ok; ut += gridDim.x, ++iter) {
-                if (!mbar_wait(&B->res_full, iter & 1, abort, a.st)) break;
+                const int rb = iter % L.nres;
+                if (!mbar_wait(&B->res_full[rb], (iter / L.nres) & 1, abort, a.st)) break;
                 tc_fence_after();
+                const uint8_t* sAr = sA + rb * L.res_bytes;
                 for (int64_t it = 0; it < item_tiles && ok; ++it) {
                     const uint32_t b = tile_j & 1u, use = tile_j >> 1;
                     if (!mbar_wait(&B->tempty[b], (use & 1u) ^ 1u, abort, a.st)) {
@@ -187,7 +197,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                             break;
                         }
                         tc_fence_after();
-                        const uint64_t ad = sdesc_sw128(smem_u32(sA + kb * KB_BYTES_U));
+                        const uint64_t ad = sdesc_sw128(smem_u32(sAr + kb * KB_BYTES_U));
                         const uint64_t bd = sdesc_sw128(smem_u32(ring + slot * KB_BYTES_I));
 #pragma unroll
                         for (int k = 0; k < 4; ++k)
@@ -203,7 +213,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                     ++tile_j;
                 }
                 if (!ok) break;
-                tc_commit(&B->res_empty);
+                tc_commit(&B->res_empty[rb]);
             }
             tc_commit(&B->drain);
             drain_wait(&B->drain, 0u, a.st);
@@ -215,6 +225,9 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         const int r = q * 32 + lane;      // user row of the tile
         float* heap = heaps + h * (a.k * BU);
         uint32_t tile_j = 0;
+        // Bound maxima of this group's first item tile (tile h of the first user tile).
+        const int64_t it0 = (h < item_tiles) ? h : 0;
+        float thm_next = a.thmax[it0], tdl_next = a.tdel[it0];
         bool ok = true;
         for (int64_t ut = blockIdx.x; ut < user_tiles && ok; ut += gridDim.x) {
             const int64_t u = ut * BU + r;
@@ -235,13 +248,21 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                 const uint32_t b = tile_j & 1u, use = tile_j >> 1;
                 ++tile_j;
                 if ((int)b != h) continue;
+                // This group's next tile is two tiles on (wrapping to the next user tile):
+                // start loading its bound maxima now.
+                const float thm = thm_next, tdl = tdl_next;
+                {
+                    const int64_t itn = (it + 2) % item_tiles;
+                    thm_next = a.thmax[itn];
+                    tdl_next = a.tdel[itn];
+                }
                 if (!mbar_wait(&B->tfull[b], use & 1u, abort, a.st)) {
                     ok = false;
                     break;
                 }
                 __syncwarp();
                 tc_fence_after();
-                const float E = err_bound(a.cacc, a.eabs, un, unh, ud, a.thmax[it], a.tdel[it]);
+                const float E = err_bound(a.cacc, a.eabs, un, unh, ud, thm, tdl);
                 // The partner's bound may be stale or from this user tile's start (-inf):
                 // any value it held is a valid lower bound of tau_u for the current user.
                 s.Lx = read_bound(&Lpub[(1 - h) * BU + r], (unsigned)ut);
@@ -304,6 +325,49 @@ __device__ __forceinline__ void decode_unit(const CountArgs& a, unsigned w, int 
     if (ut1 > all) ut1 = all;
 }
 
+// Position in a CTA's sequence of counting tiles: unit w (item tile T), user tile ut of
+// [ut0, ut1).  Units are taken as blockIdx.x, blockIdx.x + gridDim.x, ...
+struct TileCursor {
+    unsigned w;
+    int T;
+    int64_t ut, ut1;
+    bool valid;
+};
+
+__device__ __forceinline__ void cursor_unit(const CountArgs& a, unsigned total, int len, TileCursor& c) {
+    c.valid = c.w < total;
+    if (!c.valid) return;
+    int64_t ut0;
+    decode_unit(a, c.w, len, c.T, ut0, c.ut1);
+    c.ut = ut0;
+}
+
+__device__ __forceinline__ void cursor_first(const CountArgs& a, unsigned total, int len, TileCursor& c) {
+    c.w = blockIdx.x;
+    cursor_unit(a, total, len, c);
+}
+
+// Every unit holds at least one user tile, so one step never skips a unit.
+__device__ __forceinline__ void cursor_next(const CountArgs& a, unsigned total, int len, TileCursor& c) {
+    if (!c.valid) return;
+    if (++c.ut < c.ut1) return;
+    c.w += gridDim.x;
+    cursor_unit(a, total, len, c);
+}
+
+// Add a warp's per-item counters of the item tile starting at pos0 to the global counts.
+__device__ __forceinline__ void flush_counts(int* cw, int lane, int pos0, int64_t m, int* counts) {
+    __syncwarp();
+    for (int c = lane; c < BI_TC; c += 32) {
+        const int x = cw[c];
+        if (x != 0) {
+            if (pos0 + c < m) atomicAdd(&counts[pos0 + c], x);
+            cw[c] = 0;
+        }
+    }
+    __syncwarp();
+}
+
 __global__ void __launch_bounds__(TC_THREADS, 1)
     k_count_tc(const CountArgs a, const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
                const TcLayout L) {
@@ -337,10 +401,12 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                 int T;
                 int64_t ut0, ut1;
                 decode_unit(a, w, len, T, ut0, ut1);
-                if (res_loads > 0 && !mbar_wait(&B->res_empty, (res_loads - 1) & 1, abort, a.st)) break;
-                mbar_expect_tx(&B->res_full, KB * KB_BYTES_I);
+                const int rb = res_loads % L.nres, ru = res_loads / L.nres;
+                if (ru > 0 && !mbar_wait(&B->res_empty[rb], (ru - 1) & 1, abort, a.st)) break;
+                uint8_t* dst = sB + rb * L.res_bytes;
+                mbar_expect_tx(&B->res_full[rb], KB * KB_BYTES_I);
                 for (int kb = 0; kb < KB; ++kb)
-                    tma_load_2d(sB + kb * KB_BYTES_I, &tmB, &B->res_full, kb * 64, T * BI_TC);
+                    tma_load_2d(dst + kb * KB_BYTES_I, &tmB, &B->res_full[rb], kb * 64, T * BI_TC);
                 ++res_loads;
                 for (int64_t ut = ut0; ut < ut1 && ok; ++ut) {
                     for (int kb = 0; kb < KB; ++kb) {
@@ -363,7 +429,10 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             if (pairs) atomicAdd(&a.st->pairs_evaluated, pairs);
             for (int s = 0; s < S; ++s)
                 if (issued[s] > 0) drain_wait(&B->full[s], (uint32_t)(issued[s] - 1) & 1u, a.st);
-            if (res_loads > 0) drain_wait(&B->res_full, (uint32_t)(res_loads - 1) & 1u, a.st);
+            for (int rb = 0; rb < L.nres; ++rb) {
+                const int loads = res_loads / L.nres + (rb < res_loads % L.nres ? 1 : 0);
+                if (loads > 0) drain_wait(&B->res_full[rb], (uint32_t)(loads - 1) & 1u, a.st);
+            }
         }
     } else if (warp == 1) {
         if (lane == 0) {
@@ -376,8 +445,10 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                 int T;
                 int64_t ut0, ut1;
                 decode_unit(a, w, len, T, ut0, ut1);
-                if (!mbar_wait(&B->res_full, iter & 1, abort, a.st)) break;
+                const int rb = iter % L.nres;
+                if (!mbar_wait(&B->res_full[rb], (iter / L.nres) & 1, abort, a.st)) break;
                 tc_fence_after();
+                const uint8_t* sBr = sB + rb * L.res_bytes;
                 for (int64_t ut = ut0; ut < ut1 && ok; ++ut) {
                     const uint32_t b = tile_j & 1u, use = tile_j >> 1;
                     if (!mbar_wait(&B->tempty[b], (use & 1u) ^ 1u, abort, a.st)) {
@@ -393,7 +464,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                         }
                         tc_fence_after();
                         const uint64_t ad = sdesc_sw128(smem_u32(ring + slot * KB_BYTES_U));
-                        const uint64_t bd = sdesc_sw128(smem_u32(sB + kb * KB_BYTES_I));
+                        const uint64_t bd = sdesc_sw128(smem_u32(sBr + kb * KB_BYTES_I));
 #pragma unroll
                         for (int k = 0; k < 4; ++k)
                             tc_mma_bf16(d, ad + 2u * k, bd + 2u * k, idesc, (kb | k) != 0 ? 1u : 0u);
@@ -408,7 +479,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                     ++tile_j;
                 }
                 if (!ok) break;
-                tc_commit(&B->res_empty);
+                tc_commit(&B->res_empty[rb]);
             }
             tc_commit(&B->drain);
             drain_wait(&B->drain, 0u, a.st);
@@ -421,90 +492,95 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         int* cw = cnt_all + ew * BI_TC;  // this warp's per-item member counters
         for (int c = lane; c < BI_TC; c += 32) cw[c] = 0;
         __syncwarp();
-        uint32_t tile_j = 0;
-        bool ok = true;
-        for (unsigned w = blockIdx.x; w < total && ok; w += gridDim.x) {
-            int T;
-            int64_t ut0, ut1;
-            decode_unit(a, w, len, T, ut0, ut1);
-            const float pnh = a.thmax[T], pd = a.tdel[T];
-            const int pos0 = T * BI_TC;
-            for (int64_t ut = ut0; ut < ut1; ++ut) {
-                const uint32_t b = tile_j & 1u, use = tile_j >> 1;
-                ++tile_j;
-                if ((int)b != h) continue;
-                if (!mbar_wait(&B->tfull[b], use & 1u, abort, a.st)) {
-                    ok = false;
-                    break;
-                }
-                __syncwarp();
-                tc_fence_after();
-                const int64_t us = ut * BU + r;
-                const bool active = us < a.n;
-                float hi_t = 0.f, lo_t = 0.f;
-                int u_orig = 0;
-                if (active) {
-                    const float E =
-                        err_bound(a.cacc, a.eabs, a.unrm_s[us], a.unhat_s[us], a.udel_s[us], pnh, pd);
-                    const double tau = a.tau_s[us];
-                    hi_t = __fadd_ru(__double2float_ru(tau), E);
-                    lo_t = __fsub_rd(__double2float_rd(tau), E);
-                    u_orig = a.uperm[us];
-                }
-                const uint32_t tb = tmem + ((uint32_t)(q * 32) << 16) + b * BI_TC;
-                uint32_t ra[32], rb[32];
-                tmem_ld32_issue(tb, ra);
-                tmem_wait_bind(ra);
+        // This group consumes global tiles h, h+2, h+4, ... of the CTA's sequence.  `cur` is
+        // the current one, `nxt` the one after it, whose per-user record is loaded one tile
+        // ahead so that its latency hides behind the current tile.
+        TileCursor cur;
+        cursor_first(a, total, len, cur);
+        if (h == 1) cursor_next(a, total, len, cur);
+        TileCursor nxt = cur;
+        cursor_next(a, total, len, nxt);
+        cursor_next(a, total, len, nxt);
+        UserMeta um_cur{}, um_nxt{};
+        if (cur.valid && cur.ut * BU + r < a.n) um_cur = a.meta[cur.ut * BU + r];
+        uint32_t use = 0;
+        int curT = -1;
+        float pnh = 0.f, pd = 0.f;
+        while (cur.valid) {
+            if (nxt.valid && nxt.ut * BU + r < a.n) um_nxt = a.meta[nxt.ut * BU + r];
+            if (cur.T != curT) {
+                if (curT >= 0) flush_counts(cw, lane, curT * BI_TC, a.m, a.counts);
+                curT = cur.T;
+                pnh = a.thmax[cur.T];
+                pd = a.tdel[cur.T];
+            }
+            if (!mbar_wait(&B->tfull[h], use & 1u, abort, a.st)) break;
+            __syncwarp();
+            tc_fence_after();
+            const int64_t us = cur.ut * BU + r;
+            const bool active = us < a.n;
+            float hi_t = 0.f, lo_t = 0.f;
+            int u_orig = 0;
+            if (active) {
+                const float E = err_bound(a.cacc, a.eabs, um_cur.un, um_cur.unh, um_cur.ud, pnh, pd);
+                hi_t = __fadd_ru(um_cur.tau_hi, E);
+                lo_t = __fsub_rd(um_cur.tau_lo, E);
+                u_orig = um_cur.uorig;
+            }
+            const int pos0 = cur.T * BI_TC;
+            const uint32_t tb = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)h * BI_TC;
+            uint32_t ra[32], rb[32];
+            tmem_ld32_issue(tb, ra);
+            tmem_wait_bind(ra);
 #pragma unroll 1
-                for (int c0 = 0; c0 < BI_TC; c0 += 64) {
-                    __syncwarp();
-                    tmem_ld32_issue(tb + c0 + 32, rb);
-                    {
-                        float v[32];
-                        as_floats(ra, v);
-                        count_chunk(v, active, c0, pos0 + c0, a.m, hi_t, lo_t, cw, u_orig, a.band, a.band_cap,
-                                    a.st);
-                    }
-                    __syncwarp();
-                    tmem_wait_bind(rb);
-                    if (c0 + 64 < BI_TC) tmem_ld32_issue(tb + c0 + 64, ra);
-                    {
-                        float v[32];
-                        as_floats(rb, v);
-                        count_chunk(v, active, c0 + 32, pos0 + c0 + 32, a.m, hi_t, lo_t, cw, u_orig, a.band,
-                                    a.band_cap, a.st);
-                    }
-                    __syncwarp();
-                    if (c0 + 64 < BI_TC) tmem_wait_bind(ra);
-                }
-                tc_fence_before();
+            for (int c0 = 0; c0 < BI_TC; c0 += 64) {
                 __syncwarp();
-                if (lane == 0) mbar_arrive(&B->tempty[b]);
-            }
-            __syncwarp();
-            for (int c = lane; c < BI_TC; c += 32) {
-                const int x = cw[c];
-                if (x != 0) {
-                    if (pos0 + c < a.m) atomicAdd(&a.counts[pos0 + c], x);
-                    cw[c] = 0;
+                tmem_ld32_issue(tb + c0 + 32, rb);
+                {
+                    float v[32];
+                    as_floats(ra, v);
+                    count_chunk(v, active, c0, pos0 + c0, a.m, hi_t, lo_t, cw, u_orig, a.band, a.band_cap, a.st);
                 }
+                __syncwarp();
+                tmem_wait_bind(rb);
+                if (c0 + 64 < BI_TC) tmem_ld32_issue(tb + c0 + 64, ra);
+                {
+                    float v[32];
+                    as_floats(rb, v);
+                    count_chunk(v, active, c0 + 32, pos0 + c0 + 32, a.m, hi_t, lo_t, cw, u_orig, a.band,
+                                a.band_cap, a.st);
+                }
+                __syncwarp();
+                if (c0 + 64 < BI_TC) tmem_wait_bind(ra);
             }
+            tc_fence_before();
             __syncwarp();
+            if (lane == 0) mbar_arrive(&B->tempty[h]);
+            ++use;
+            cur = nxt;
+            um_cur = um_nxt;
+            cursor_next(a, total, len, nxt);
+            cursor_next(a, total, len, nxt);
         }
+        if (curT >= 0) flush_counts(cw, lane, curT * BI_TC, a.m, a.counts);
     }
     teardown(B, warp);
 }
 
+// Shared-memory plan: two resident buffers when that still leaves two ring slots, else one;
+// then as many ring slots (up to max_slots) as fit in the 227 KB opt-in limit.
 TcLayout make_layout(uint32_t res_bytes, uint32_t slot_bytes, uint32_t aux_bytes, int max_slots) {
     TcLayout L{};
-    L.res_off = 0;
-    L.ring_off = res_bytes;
-    L.slot_bytes = slot_bytes;
     aux_bytes = (aux_bytes + 1023u) & ~1023u;
-    const uint32_t fixed = 1024u + res_bytes + aux_bytes + 1024u;  // align slack + barriers
+    const uint32_t fixed = 1024u + aux_bytes + 1024u;  // align slack + barriers
+    L.nres = (fixed + 2u * res_bytes + 2u * slot_bytes <= (uint32_t)SMEM_LIMIT) ? 2 : 1;
     int slots = max_slots;
-    while (slots > 1 && fixed + slots * slot_bytes > (uint32_t)SMEM_LIMIT) --slots;
+    while (slots > 1 && fixed + L.nres * res_bytes + slots * slot_bytes > (uint32_t)SMEM_LIMIT) --slots;
     L.slots = slots;
+    L.res_bytes = res_bytes;
+    L.slot_bytes = slot_bytes;
+    L.res_off = 0;
+    L.ring_off = L.nres * res_bytes;
     L.aux_off = L.ring_off + slots * slot_bytes;
     L.bar_off = L.aux_off + aux_bytes;
     L.bytes = 1024u + L.bar_off + (uint32_t)sizeof(TcBars);
