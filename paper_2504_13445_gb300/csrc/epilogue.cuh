@@ -40,6 +40,7 @@ __device__ __forceinline__ void heap_replace_root(float* heap, int t, int k, flo
 }
 
 static __device__ __noinline__ int compact_candidates(Cand* c, int cnt, float L) {
+    // Keep the candidates whose upper bound still reaches the bound L <= tau_u.
     int w = 0;
     for (int r = 0; r < cnt; ++r) {
         Cand x = c[r];
@@ -49,16 +50,21 @@ static __device__ __noinline__ int compact_candidates(Cand* c, int cnt, float L)
 }
 
 struct SelState {
-    float L;     // root of the lower-bound heap (k-th largest v - E so far)
+    float L;     // heap root once the heap holds k lower bounds (-inf while it fills)
+    int hn;      // lower bounds held in the heap (<= k)
+    float Lw;    // warm-start bound of this group (-inf if none)
     float Lx;    // a lower bound of tau_u published by the other epilogue group (or -inf)
-    float thr;   // max(L, Lx) - E of the current tile, rounded down
+    float thr;   // max(L, Lw, Lx) - E of the current tile, rounded down
     int cnt;     // candidates stored
-    unsigned long long* pub;  // where this group publishes L for the other group (null: none)
+    unsigned long long* pub;  // where this group publishes its bound for the other (null: none)
     unsigned tag;             // user tile the published bound belongs to
 };
 
-// A published bound: (user tile << 32) | bits of L, written and read as one 64-bit word so a
-// reader never mixes a bound with the tag of another user tile.
+// The best lower bound of tau_u this group knows.
+__device__ __forceinline__ float sel_bound(const SelState& s) { return fmaxf(fmaxf(s.L, s.Lw), s.Lx); }
+
+// A published bound: (user tile << 32) | bits of the bound, written and read as one 64-bit
+// word so a reader never mixes a bound with the tag of another user tile.
 __device__ __forceinline__ void publish_bound(unsigned long long* p, unsigned tag, float L) {
     *reinterpret_cast<volatile unsigned long long*>(p) =
         ((unsigned long long)tag << 32) | (unsigned long long)__float_as_uint(L);
@@ -69,11 +75,38 @@ __device__ __forceinline__ float read_bound(const unsigned long long* p, unsigne
     return ((unsigned)(x >> 32) == tag) ? __uint_as_float((unsigned)(x & 0xffffffffull)) : -INFINITY;
 }
 
+// Min-heap order over heap[0 .. k) of user-thread t (bottom-up construction).
+__device__ __forceinline__ void heapify(float* heap, int t, int k) {
+    for (int i = k / 2 - 1; i >= 0; --i) {
+        const float v = heap[i * BU + t];
+        int j = i;
+        while (true) {
+            const int l = 2 * j + 1;
+            if (l >= k) break;
+            int c = l;
+            float cv = heap[l * BU + t];
+            if (l + 1 < k) {
+                const float rv = heap[(l + 1) * BU + t];
+                if (rv < cv) { c = l + 1; cv = rv; }
+            }
+            if (cv >= v) break;
+            heap[j * BU + t] = cv;
+            j = c;
+        }
+        heap[j * BU + t] = v;
+    }
+}
+
+// Record a value that reached the threshold: store it as a candidate (with its upper bound),
+// and admit its lower bound into the heap when it raises the best bound known here.  Any k
+// lower bounds held in the heap make its root a valid lower bound of tau_u, so skipping an
+// admission is sound; while the heap fills, admission is an append, and the heap is built
+// once when it holds k values.
 __device__ __forceinline__ void sel_insert(float v, int pos, float E, SelState& s, Cand* mycand, int cap,
                                            float* heap, int t, int k, DevStatus* st) {
     const float ub = __fadd_ru(v, E);
     const float lb = __fsub_rd(v, E);
-    if (s.cnt >= cap) s.cnt = compact_candidates(mycand, s.cnt, fmaxf(s.L, s.Lx));
+    if (s.cnt >= cap) s.cnt = compact_candidates(mycand, s.cnt, sel_bound(s));
     if (s.cnt < cap) {
         Cand c;
         c.ub = ub;
@@ -82,11 +115,17 @@ __device__ __forceinline__ void sel_insert(float v, int pos, float E, SelState& 
     } else {
         st->cand_overflow = 1u;
     }
-    if (lb > s.L) {
-        heap_replace_root(heap, t, k, lb);
+    if (lb > sel_bound(s)) {
+        if (s.hn < k) {
+            heap[s.hn * BU + t] = lb;
+            if (++s.hn < k) return;
+            heapify(heap, t, k);
+        } else {
+            heap_replace_root(heap, t, k, lb);
+        }
         s.L = heap[t];
-        if (s.pub) publish_bound(s.pub, s.tag, s.L);
-        s.thr = __fsub_rd(fmaxf(s.L, s.Lx), E);
+        if (s.pub) publish_bound(s.pub, s.tag, fmaxf(s.L, s.Lw));
+        s.thr = __fsub_rd(sel_bound(s), E);
     }
 }
 
@@ -172,6 +211,50 @@ __device__ __forceinline__ void count_chunk(const float (&v)[32], bool active, i
             else st->band_overflow = 1u;
         }
     }
+}
+
+// Warm-start bound from COLS columns of one accumulator row held in TMEM: the maxima of
+// the NG column groups of width COLS/NG, sorted by a bitonic network in registers; the k-th
+// largest (k <= NG) minus E bounds tau_u from below, because k distinct items reach it.
+// Columns at or beyond m count as -inf.  Returns -inf when fewer than k groups are valid.
+template <int NG, int COLS, typename LoadChunk>
+__device__ __forceinline__ float warm_bound(LoadChunk load, int pos0, int64_t m, int k, float E) {
+    constexpr int GW = COLS / NG;  // group width
+    float g[NG];
+#pragma unroll
+    for (int c0 = 0; c0 < COLS; c0 += 32) {
+        float v[32];
+        load(c0, v);
+#pragma unroll
+        for (int q = 0; q < 32 / GW; ++q) {
+            float x = -INFINITY;
+#pragma unroll
+            for (int j = 0; j < GW; ++j)
+                if (pos0 + c0 + q * GW + j < m) x = fmaxf(x, v[q * GW + j]);
+            g[(c0 / GW) + q] = x;
+        }
+    }
+#pragma unroll
+    for (int size = 2; size <= NG; size <<= 1) {
+#pragma unroll
+        for (int stride = size >> 1; stride > 0; stride >>= 1) {
+#pragma unroll
+            for (int i = 0; i < NG; ++i) {
+                const int j = i ^ stride;
+                if (j > i) {
+                    const float hi = fmaxf(g[i], g[j]), lo = fminf(g[i], g[j]);
+                    const bool desc = (i & size) == 0;
+                    g[i] = desc ? hi : lo;
+                    g[j] = desc ? lo : hi;
+                }
+            }
+        }
+    }
+    float kth = -INFINITY;
+#pragma unroll
+    for (int j = 0; j < NG; ++j)
+        if (j == k - 1) kth = g[j];
+    return (kth == -INFINITY) ? -INFINITY : __fsub_rd(kth, E);
 }
 
 }  // namespace rkm

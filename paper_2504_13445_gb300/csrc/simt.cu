@@ -108,6 +108,8 @@ __global__ void __launch_bounds__(SIMT_THREADS, 1) k_threshold_simt(ThresholdArg
         const bool active = owner && u < a.n;
         SelState s;
         s.L = -INFINITY;
+        s.hn = 0;
+        s.Lw = -INFINITY;
         s.Lx = -INFINITY;
         s.thr = -INFINITY;
         s.cnt = 0;
@@ -128,7 +130,7 @@ __global__ void __launch_bounds__(SIMT_THREADS, 1) k_threshold_simt(ThresholdArg
             simt_tile(A, ut * BU, B, it * BI_SIMT, a.dp, sm);
             if (owner) {
                 const float E = err_bound(a.cacc, a.eabs, un, unh, ud, a.thmax[it], a.tdel[it]);
-                s.thr = __fsub_rd(fmaxf(s.L, s.Lx), E);
+                s.thr = __fsub_rd(sel_bound(s), E);
 #pragma unroll 1
                 for (int c0 = 0; c0 < BI_SIMT; c0 += 32) {
                     float v[32];
@@ -140,7 +142,7 @@ __global__ void __launch_bounds__(SIMT_THREADS, 1) k_threshold_simt(ThresholdArg
             __syncthreads();
         }
         if (active) {
-            atomicMax(&a.lfin_key[u], float_key(s.L));
+            atomicMax(&a.lfin_key[u], float_key(fmaxf(s.L, s.Lw)));
             a.cand_cnt[u * a.nseg] = s.cnt;
         }
     }

@@ -235,11 +235,14 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             for (int j = 0; j < a.k; ++j) heap[j * BU + r] = -INFINITY;
             SelState s;
             s.L = -INFINITY;
+            s.hn = 0;
+            s.Lw = -INFINITY;
             s.Lx = -INFINITY;
             s.thr = -INFINITY;
             s.cnt = 0;
             s.pub = &Lpub[h * BU + r];
             s.tag = (unsigned)ut;
+            bool warm = false;  // warm start done for this user tile
             const float un = active ? a.unrm[u] : 0.f;
             const float unh = active ? a.unhat[u] : 0.f;
             const float ud = active ? a.udel[u] : 0.f;
@@ -252,7 +255,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                 // start loading its bound maxima now.
                 const float thm = thm_next, tdl = tdl_next;
                 {
-                    const int64_t itn = (it + 2) % item_tiles;
+                    int itn = (int)it + 2;
+                    while (itn >= (int)item_tiles) itn -= (int)item_tiles;
                     thm_next = a.thmax[itn];
                     tdl_next = a.tdel[itn];
                 }
@@ -266,8 +270,24 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                 // The partner's bound may be stale or from this user tile's start (-inf):
                 // any value it held is a valid lower bound of tau_u for the current user.
                 s.Lx = read_bound(&Lpub[(1 - h) * BU + r], (unsigned)ut);
-                s.thr = __fsub_rd(fmaxf(s.L, s.Lx), E);
                 const uint32_t tb = tmem + ((uint32_t)(q * 32) << 16) + b * BI_TC;
+                if (!warm) {
+                    // First tile of this group for these users: a lockstep first pass over the
+                    // accumulator gives a lower bound before any candidate is recorded, so the
+                    // heap does not fill one divergent insertion at a time.  (For k > 32 the
+                    // heap fills from the candidates alone.)
+                    if (a.k <= 32) {
+                        auto load = [&](int c0, float (&v)[32]) {
+                            __syncwarp();
+                            tmem_ld32(tb + c0, v);
+                        };
+                        const float lw = warm_bound<32, BI_TC>(load, (int)(it * BI_TC), a.m, a.k, E);
+                        s.Lw = active ? lw : -INFINITY;
+                        publish_bound(s.pub, s.tag, s.Lw);
+                    }
+                    warm = true;
+                }
+                s.thr = __fsub_rd(sel_bound(s), E);
                 // Two register buffers: the load of the next 32 columns overlaps the current chunk.
                 uint32_t ra[32], rb[32];
                 tmem_ld32_issue(tb, ra);
@@ -299,7 +319,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                 if (lane == 0) mbar_arrive(&B->tempty[b]);
             }
             if (active) {
-                atomicMax(&a.lfin_key[u], float_key(s.L));
+                atomicMax(&a.lfin_key[u], float_key(fmaxf(s.L, s.Lw)));
                 a.cand_cnt[u * a.nseg + h] = s.cnt;
             }
         }
