@@ -195,6 +195,24 @@ RKM_API rkm_status rkm_query_new_items(rkm_ctx* ctx, const float* Q, int64_t q, 
 /* Counters of the last call. */
 RKM_API rkm_status rkm_get_stats(const rkm_ctx* ctx, rkm_stats* out);
 
+/*
+ * Top-N of a score array without allocating device memory (the paper has no counterpart:
+ * this is a library service).  For callers that cannot call cudaMalloc -- a process that
+ * reserves all device memory up front and forbids later allocations, or code that runs
+ * inside another library's memory manager with only the buffers it was given.
+ *   scores: device [m] int32 (e.g. from rkm_scores), 1 <= m < 2^31.
+ *   ids, top_scores: device [N] int32, filled in order (score descending, id ascending),
+ *   1 <= N <= min(m, 4096); a larger N returns RKM_EINVAL.
+ * No context: the only scratch is a fixed 32 KB device array inside the library (one per
+ * device that loads it, kept until the process exits); nothing is allocated or freed.  The
+ * first call on a device looks up that array's address (a runtime call), so make it before
+ * any stream capture on that device.  Every call shares the array and clears what it needs;
+ * calls that overlap on the GPU race on it and must be serialised by the caller.  The call
+ * synchronises `stream` to read its status word.
+ */
+RKM_API rkm_status rkm_topn_scores_noalloc(const int32_t* scores, int64_t m, int N, int32_t* ids,
+                                           int32_t* top_scores, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

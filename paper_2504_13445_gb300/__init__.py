@@ -22,7 +22,7 @@ STATUS = {0: "RKM_OK", 1: "RKM_EINVAL", 2: "RKM_ENOMEM", 3: "RKM_ECUDA", 4: "RKM
 
 EXPORTED = ["rkm_default_opts", "rkm_create", "rkm_destroy", "rkm_last_error", "rkm_version",
             "rkm_thresholds", "rkm_scores", "rkm_topn", "rkm_topn_host", "rkm_item_bounds",
-            "rkm_resident_set", "rkm_query_new_items", "rkm_get_stats"]
+            "rkm_resident_set", "rkm_query_new_items", "rkm_get_stats", "rkm_topn_scores_noalloc"]
 
 
 class RkmError(RuntimeError):
@@ -78,6 +78,7 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         "rkm_resident_set": (I, [P, P, I64, I64, I, P, P, P]),
         "rkm_query_new_items": (I, [P, P, I64, I64, P, P]),
         "rkm_get_stats": (I, [P, ctypes.POINTER(Stats)]),
+        "rkm_topn_scores_noalloc": (I, [P, I64, I, P, P, P]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -211,6 +212,19 @@ def rkm_get_stats(ctx) -> dict:
     s = Stats()
     _check(load_library().rkm_get_stats(ctx, ctypes.byref(s)))
     return s.as_dict()
+
+
+def rkm_topn_scores_noalloc(scores, N: int):
+    """Top N of a device int32 score array through the entry point that allocates no device
+    memory (for callers that cannot call cudaMalloc); the output tensors are allocated here,
+    by the caller's side, as the C ABI expects."""
+    import torch
+    scores = scores.contiguous()
+    ids = torch.empty(N, dtype=torch.int32, device=scores.device)
+    top = torch.empty(N, dtype=torch.int32, device=scores.device)
+    _check(load_library().rkm_topn_scores_noalloc(_ptr(scores), scores.numel(), N, _ptr(ids), _ptr(top),
+                                                  _stream()))
+    return ids, top
 
 
 def rkm_version() -> str:

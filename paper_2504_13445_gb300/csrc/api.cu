@@ -48,6 +48,15 @@ rkm_status fail(rkm_status s, const char* fmt, ...) {
     return s;
 }
 
+}  // namespace
+
+int rkm::set_error(int s, const char* msg) {
+    g_err = msg;
+    return s;
+}
+
+namespace {
+
 #define CUDA_TRY(expr)                                                                        \
     do {                                                                                      \
         cudaError_t e_ = (expr);                                                              \

@@ -10,6 +10,9 @@
 
 namespace rkm {
 
+// Record the message returned by rkm_last_error() on this host thread; returns s.
+int set_error(int s, const char* msg);
+
 // Kernels launched by this library since load (each launcher calls note_launch()).
 extern std::atomic<unsigned long long> g_launches;
 inline void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
