@@ -1,0 +1,77 @@
+"""Parity at the benchmark's full sizes, in the launch configuration bench.py times.
+
+The oracle cannot score 5e10 (or 1e12) pairs in a test, so:
+* tau_u, t_u and S_k(u) are compared bit for bit on a seeded sample of users that the
+  oracle rescores one by one against every item;
+* the scores satisfy sum(score) = n*k, and the two Section 2.2 formulations agree on the
+  GPU (histogram of S_k(u) from rkm_thresholds vs per-item counting from rkm_scores);
+* the filtered top-N of rkm_topn equals the top-N of the full score vector (the Eq. 2
+  filter never changes the answer), and the Eq. 2 bound dominates every score (Theorem 2);
+* the BF16 tensor-core path and the FP32 CUDA-core path return identical integers.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import workloads
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def rkm():
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_2504_13445_gb300 as m
+    return m
+
+
+def sample_users(n, count, seed):
+    rng = np.random.default_rng(seed)
+    return np.unique(np.r_[0, n - 1, rng.integers(0, n, size=count)])
+
+
+def check_full(rkm, W, prec, sample, check_fp32=False):
+    U = torch.from_numpy(W.U).cuda()
+    P = torch.from_numpy(W.P).cuda()
+    with rkm.Context(prec) as ctx:
+        ids, tops, tau, tid = ctx.topn(U, P, W.k, W.N, return_thresholds=True)
+        tau2, tid2, topk = ctx.thresholds(U, P, W.k, want_topk=True)
+        scores = ctx.scores(U, P, tau2, tid2)
+        us = ctx.item_bounds(U, P, tau2)
+    tau, tid, tau2, tid2 = (x.cpu().numpy() for x in (tau, tid, tau2, tid2))
+    topk = topk.cpu().numpy()
+    scores = scores.cpu().numpy().astype(np.int64)
+    us = us.cpu().numpy().astype(np.int64)
+    # the same thresholds from both entry points
+    np.testing.assert_array_equal(tau.view(np.uint64), tau2.view(np.uint64))
+    np.testing.assert_array_equal(tid, tid2)
+    # sampled users against the oracle
+    t_o, i_o, k_o = oracle.kmips(W.U[sample], W.P, W.k, block=64)
+    np.testing.assert_array_equal(tau[sample].view(np.uint64), t_o.view(np.uint64))
+    np.testing.assert_array_equal(tid[sample], i_o)
+    np.testing.assert_array_equal(topk[sample], k_o)
+    # invariants of the scores
+    assert int(scores.sum()) == W.n * W.k
+    np.testing.assert_array_equal(scores, np.bincount(topk.ravel(), minlength=W.m))
+    assert np.all(us >= scores)
+    ids_o, tops_o = oracle.topn(scores, W.N)
+    np.testing.assert_array_equal(ids.cpu().numpy(), ids_o)
+    np.testing.assert_array_equal(tops.cpu().numpy(), tops_o)
+    if check_fp32:
+        with rkm.Context("fp32") as c32:
+            i32, s32, t32, d32 = c32.topn(U, P, W.k, W.N, return_thresholds=True)
+        np.testing.assert_array_equal(t32.cpu().numpy().view(np.uint64), tau.view(np.uint64))
+        np.testing.assert_array_equal(d32.cpu().numpy(), tid)
+        np.testing.assert_array_equal(i32.cpu().numpy(), ids_o)
+
+
+def test_mf_500k_full_size_bf16_and_fp32_identical(rkm):
+    W = workloads.make("mf-500k")
+    check_full(rkm, W, "bf16", sample_users(W.n, 300, 1), check_fp32=True)
+
+
+def test_mf_2m_k50_full_size(rkm):
+    W = workloads.make("mf-2m-k50")
+    check_full(rkm, W, "bf16", sample_users(W.n, 100, 2))

@@ -194,3 +194,22 @@ def test_invalid_arguments(rkm):
             ctx.topn(dev(W.U), dev(W.P), 2, 0)          # N < 1
         with pytest.raises(rkm.RkmError):
             ctx.query_new_items(dev(W.P))               # no resident users
+
+
+@pytest.mark.parametrize("prec", PRECISIONS)
+def test_adversarial_cancellation_rows(rkm, prec):
+    """Rows whose products cancel almost completely: u . p is tiny next to ||u|| ||p||, the
+    regime where BF16 rounding of the operands is largest relative to the scores, with many
+    near-ties around tau_u.  The guard band must still give exact results."""
+    rng = np.random.default_rng(77)
+    d, n, m = 64, 600, 900
+    base = rng.integers(1000, 4096, size=(1, d)).astype(np.float64)
+    signs = np.where(np.arange(d) % 2 == 0, 1.0, -1.0)
+    U = (base + rng.integers(-3, 4, size=(n, d))) / 4096
+    P = (base * signs + rng.integers(-3, 4, size=(m, d))) / 4096
+    P *= np.ldexp(1.0, rng.integers(-2, 2, size=(m, 1)))
+    U = np.clip(U, -1, 1).astype(np.float32)
+    P = np.clip(P, -2, 2).astype(np.float32)
+    assert oracle.on_grid(U) and oracle.on_grid(P)
+    with rkm.Context(prec) as ctx:
+        full_check(ctx, U, P, 20, 30)
