@@ -352,11 +352,76 @@ def run_ours(args, rank, local, world):
     print(json.dumps(line), flush=True)
 
 
+def run_batch(args, rank, local, world):
+    """The 64-instance batch (users log-uniform in [1e4, 1e6], items in [5e3, 2e5], d in
+    {32, 64, 128}, k in {5, 10, 25}, N = 20): one rkm_topn_batch per step, BF16, autotuned
+    counting tiles, graph replayed after the first call."""
+    import tempfile
+
+    import torch
+
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_2504_13445_gb300 as rkm
+    import workloads
+
+    torch.cuda.set_device(local)
+    sizes = workloads.batching_instances(64)
+    if args.n:  # shrink every instance (smoke runs)
+        sizes = [dict(sz, n=max(64, sz["n"] // args.n), m=max(64, sz["m"] // args.n)) for sz in sizes]
+    probs = []
+    for sz in sizes:
+        W = workloads.mf(sz["n"], sz["m"], sz["d"], sz["k"], sz["N"], seed=sz["seed"])
+        probs.append((torch.from_numpy(W.U).cuda(), torch.from_numpy(W.P).cuda(), W.k, W.N))
+    pairs = sum(sz["n"] * sz["m"] for sz in sizes)
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device="cuda")
+    cache = os.path.join(tempfile.gettempdir(), "rkm_tune_cache.txt")
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        ctx = rkm.Context(args.precision, device=local, autotune=True, tune_cache=cache)
+        outs = None
+        for _ in range(args.warmup):
+            outs = ctx.topn_batch(probs, outs)
+        torch.cuda.synchronize()
+        clocks = ClockSampler(local)
+        barrier(world)
+        clocks.start()
+        step_ms, launches = [], 0
+        for _ in range(args.steps):
+            flush.zero_()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            outs = ctx.topn_batch(probs, outs)
+            e1.record(stream)
+            e1.synchronize()
+            step_ms.append(e0.elapsed_time(e1))
+            launches += ctx.stats()["kernel_launches"]
+        clk = clocks.stop()
+        barrier(world)
+    ms = max_over_ranks(sum(step_ms), world) / args.steps
+    if rank != 0:
+        return
+    line = {"metric": METRIC, "value": world * pairs / (ms / 1000), "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "bf16" if args.precision == "bf16" else "f32",
+            "data": "synthetic",
+            "config": {"workload": "batch-64", "instances": len(sizes), "pairs": pairs,
+                       "users": sum(sz["n"] for sz in sizes), "items": sum(sz["m"] for sz in sizes),
+                       "precision": args.precision, "graph": "captured on the first call, replayed",
+                       "autotune": "counting work-unit size and first-stage size per size bucket",
+                       "l2": "flushed (512 MiB write) before each timed step"},
+            "roofline": None, "gpu_launches": int(launches), "clocks": clk}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     rank, local, world = dist_init()
     if args.impl == "reference":
         run_reference(args, rank, world)
+    elif args.workload == "batch-64":
+        run_batch(args, rank, local, world)
     else:
         run_ours(args, rank, local, world)
     if world > 1:

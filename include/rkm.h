@@ -78,6 +78,9 @@ typedef struct {
     int64_t band_capacity;   /* initial band-queue capacity in pairs (0 = auto)    */
     int filter;              /* rkm_topn: 1 = Eq. 2 item filter (default), 0 = off */
     int profile;             /* 1 = time each phase with CUDA events (rkm_stats)   */
+    int autotune;            /* rkm_topn_batch: 1 = tune the counting tiles per size
+                                bucket on first sight (default 0)                    */
+    const char* tune_cache;  /* file that keeps autotuned choices across runs, or NULL */
 } rkm_opts;
 
 /* Phases timed when rkm_opts.profile is set (indices of rkm_stats.phase_ms). */
@@ -194,6 +197,31 @@ RKM_API rkm_status rkm_query_new_items(rkm_ctx* ctx, const float* Q, int64_t q, 
 
 /* Counters of the last call. */
 RKM_API rkm_status rkm_get_stats(const rkm_ctx* ctx, rkm_stats* out);
+
+/* One problem of a batch: device inputs and outputs as for rkm_topn. */
+typedef struct {
+    const float* U;
+    int64_t n, ldu;
+    const float* P;
+    int64_t m, ldp;
+    int d, k, N;
+    int32_t* ids;         /* device [N] */
+    int32_t* top_scores;  /* device [N] */
+} rkm_instance;
+
+/*
+ * Batch of independent top-N problems (Definition 3 for each).  The tensor-core threshold
+ * products of all instances run in one persistent launch (work units = user tiles of every
+ * instance, largest instances first); the whole sequence of kernels is captured into a CUDA
+ * graph on the first call with a given batch layout (same pointers, sizes and options) and
+ * replayed by later calls with that layout.  Results equal rkm_topn on each instance: an
+ * instance whose candidate or band buffers overflow inside the graph is recomputed by the
+ * retrying single-instance path (and the graph is rebuilt on the next call).  With
+ * opts.autotune, the first sight of a size bucket (d, k, log2 n, log2 m) times the counting
+ * pass's work-unit size and first-stage size on that instance and keeps the fastest (in
+ * opts.tune_cache when given).  1 <= count <= 4096.  Synchronises `stream`.
+ */
+RKM_API rkm_status rkm_topn_batch(rkm_ctx* ctx, const rkm_instance* inst, int count, void* stream);
 
 /*
  * Top-N of a score array without allocating device memory (the paper has no counterpart:

@@ -22,7 +22,8 @@ STATUS = {0: "RKM_OK", 1: "RKM_EINVAL", 2: "RKM_ENOMEM", 3: "RKM_ECUDA", 4: "RKM
 
 EXPORTED = ["rkm_default_opts", "rkm_create", "rkm_destroy", "rkm_last_error", "rkm_version",
             "rkm_thresholds", "rkm_scores", "rkm_topn", "rkm_topn_host", "rkm_item_bounds",
-            "rkm_resident_set", "rkm_query_new_items", "rkm_get_stats", "rkm_topn_scores_noalloc"]
+            "rkm_resident_set", "rkm_query_new_items", "rkm_get_stats", "rkm_topn_scores_noalloc",
+            "rkm_topn_batch"]
 
 
 class RkmError(RuntimeError):
@@ -33,7 +34,15 @@ class RkmError(RuntimeError):
 
 class Opts(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int), ("k_max", ctypes.c_int), ("cand_capacity", ctypes.c_int),
-                ("band_capacity", ctypes.c_int64), ("filter", ctypes.c_int), ("profile", ctypes.c_int)]
+                ("band_capacity", ctypes.c_int64), ("filter", ctypes.c_int), ("profile", ctypes.c_int),
+                ("autotune", ctypes.c_int), ("tune_cache", ctypes.c_char_p)]
+
+
+class Instance(ctypes.Structure):
+    _fields_ = [("U", ctypes.c_void_p), ("n", ctypes.c_int64), ("ldu", ctypes.c_int64),
+                ("P", ctypes.c_void_p), ("m", ctypes.c_int64), ("ldp", ctypes.c_int64),
+                ("d", ctypes.c_int), ("k", ctypes.c_int), ("N", ctypes.c_int),
+                ("ids", ctypes.c_void_p), ("top_scores", ctypes.c_void_p)]
 
 
 class Stats(ctypes.Structure):
@@ -79,6 +88,7 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         "rkm_query_new_items": (I, [P, P, I64, I64, P, P]),
         "rkm_get_stats": (I, [P, ctypes.POINTER(Stats)]),
         "rkm_topn_scores_noalloc": (I, [P, I64, I, P, P, P]),
+        "rkm_topn_batch": (I, [P, ctypes.POINTER(Instance), I, P]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -115,7 +125,8 @@ def _mat(X):
 # ---------------------------------------------------------------- C-ABI names
 
 def rkm_create(precision: str = "bf16", device: int = 0, k_max: int = 64, cand_capacity: int = 0,
-               band_capacity: int = 0, filter: bool = True, profile: bool = False) -> ctypes.c_void_p:
+               band_capacity: int = 0, filter: bool = True, profile: bool = False, autotune: bool = False,
+               tune_cache: str | None = None) -> ctypes.c_void_p:
     lib = load_library()
     o = Opts()
     lib.rkm_default_opts(ctypes.byref(o))
@@ -125,6 +136,8 @@ def rkm_create(precision: str = "bf16", device: int = 0, k_max: int = 64, cand_c
     o.band_capacity = band_capacity
     o.filter = 1 if filter else 0
     o.profile = 1 if profile else 0
+    o.autotune = 1 if autotune else 0
+    o.tune_cache = tune_cache.encode() if tune_cache else None
     h = ctypes.c_void_p()
     _check(lib.rkm_create(ctypes.byref(h), ctypes.byref(o), device))
     return h
@@ -214,6 +227,29 @@ def rkm_get_stats(ctx) -> dict:
     return s.as_dict()
 
 
+def rkm_topn_batch(ctx, problems, outs=None):
+    """problems: list of (U, P, k, N) with float32 CUDA matrices.  Returns [(ids, scores)].
+    Pass the previous result as `outs` to reuse the output buffers (a batch with the same
+    inputs and outputs replays the library's captured graph)."""
+    import torch
+    arr = (Instance * len(problems))()
+    new_outs, keep = [], []
+    for j, (U, P, k, N) in enumerate(problems):
+        U, n, ldu = _mat(U)
+        P, m, ldp = _mat(P)
+        if outs is not None:
+            ids, sc = outs[j]
+        else:
+            ids = torch.empty(N, dtype=torch.int32, device=U.device)
+            sc = torch.empty(N, dtype=torch.int32, device=U.device)
+        keep += [U, P]
+        new_outs.append((ids, sc))
+        arr[j] = Instance(U.data_ptr(), n, ldu, P.data_ptr(), m, ldp, U.shape[1], k, N, ids.data_ptr(),
+                          sc.data_ptr())
+    _check(load_library().rkm_topn_batch(ctx, arr, len(problems), _stream()))
+    return new_outs
+
+
 def rkm_topn_scores_noalloc(scores, N: int):
     """Top N of a device int32 score array through the entry point that allocates no device
     memory (for callers that cannot call cudaMalloc); the output tensors are allocated here,
@@ -263,6 +299,9 @@ class Context:
 
     def topn(self, U, P, k, N, return_thresholds=False):
         return rkm_topn(self.handle, U, P, k, N, return_thresholds)
+
+    def topn_batch(self, problems, outs=None):
+        return rkm_topn_batch(self.handle, problems, outs)
 
     def topn_host(self, U, P, k, N):
         return rkm_topn_host(self.handle, U, P, k, N)

@@ -19,6 +19,9 @@
 #include <string>
 #include <vector>
 #include <atomic>
+#include <map>
+#include <fstream>
+#include <sstream>
 
 #include "../../include/rkm.h"
 #include "common.cuh"
@@ -96,7 +99,7 @@ struct rkm_ctx {
     bool resident = false;
     int64_t res_n = 0;
     int res_d = 0;
-    unsigned res_grid = 0;
+    unsigned res_off_grid = 0;
     Buf res_U, res_e, res_q, res_tau, res_tid, res_uperm, res_ucum, res_pack, res_meta;
     // query scratch
     Buf q_e, q_q, q_n2, q_nrm, q_nhat, q_del, q_perm, q_pack, q_tmax, q_thmax, q_tdel, q_cnt;
@@ -104,6 +107,28 @@ struct rkm_ctx {
     Buf h_U, h_P, h_ids, h_sc;
     int cand_cap = 0;
     int cand_k = 0;
+    // Batches: one sub-context per instance (its own workspace and status), the captured graph
+    // and the layout it was captured for, the batch's launch descriptors.
+    std::vector<rkm_ctx*> sub;
+    std::vector<rkm_instance> graph_key;
+    int graph_opts_key = 0;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t graph_exec = nullptr;
+    unsigned long long graph_kernels = 0;
+    TcInstance* batch_host = nullptr;
+    int batch_host_cap = 0;
+    Buf batch_dev;
+    std::string tune_cache;
+    std::map<std::string, std::pair<int, int64_t>> tune;  // size bucket -> (group, first-stage items)
+    bool tune_loaded = false;
+    // Batches run on an internal stream joined to the caller's stream by events, so that the
+    // graph can be captured whatever stream the caller uses.
+    cudaStream_t bstream = nullptr;
+    cudaEvent_t bev_in = nullptr, bev_out = nullptr;
+    // Tunables (set by the autotuner for batches): user tiles per counting work unit, and the
+    // minimum number of items in the first counting stage of the filtered top-N.
+    int count_group = 32;
+    int64_t stage1_items = 8192;
     int64_t band_cap = 0;
     // phase timing (opts.profile)
     struct Pending {
@@ -123,6 +148,26 @@ struct rkm_ctx {
         cudaEvent_t e = ev_pool.back();
         ev_pool.pop_back();
         return e;
+    }
+
+    // Descriptors of the tensor-core threshold launch: pinned host staging and device copy.
+    TcInstance* inst_host = nullptr;
+    int inst_host_cap = 0;
+    Buf inst_dev;
+
+    rkm_status instances(int count, TcInstance** host, TcInstance** dev) {
+        if (inst_host_cap < count) {
+            if (inst_host) cudaFreeHost(inst_host);
+            inst_host = nullptr;
+            inst_host_cap = 0;
+            if (cudaMallocHost(&inst_host, (size_t)count * sizeof(TcInstance)) != cudaSuccess) {
+                cudaGetLastError();
+                return fail(RKM_ENOMEM, "pinned descriptor staging of %d instances failed", count);
+            }
+            inst_host_cap = count;
+        }
+        *host = inst_host;
+        return ensure(inst_dev, count, dev);
     }
 
     template <typename T>
@@ -166,6 +211,25 @@ struct rkm_ctx {
         pending.clear();
         for (cudaEvent_t e : ev_pool) cudaEventDestroy(e);
         ev_pool.clear();
+        if (inst_dev.p) cudaFree(inst_dev.p);
+        inst_dev = Buf{};
+        if (inst_host) cudaFreeHost(inst_host);
+        inst_host = nullptr;
+        inst_host_cap = 0;
+        if (graph_exec) cudaGraphExecDestroy(graph_exec);
+        if (graph) cudaGraphDestroy(graph);
+        graph_exec = nullptr;
+        graph = nullptr;
+        if (batch_dev.p) cudaFree(batch_dev.p);
+        batch_dev = Buf{};
+        if (bstream) cudaStreamDestroy(bstream);
+        if (bev_in) cudaEventDestroy(bev_in);
+        if (bev_out) cudaEventDestroy(bev_out);
+        bstream = nullptr;
+        bev_in = bev_out = nullptr;
+        if (batch_host) cudaFreeHost(batch_host);
+        batch_host = nullptr;
+        batch_host_cap = 0;
     }
 };
 
@@ -273,8 +337,6 @@ rkm_status check_common(rkm_ctx* c, int d) {
 
 rkm_status begin_call(rkm_ctx* c, cudaStream_t s) {
     CUDA_TRY(cudaMemsetAsync(c->st, 0, sizeof(DevStatus), s));
-    const unsigned one = 1u;
-    CUDA_TRY(cudaMemcpyAsync(&c->st->grid_u, &one, sizeof(unsigned), cudaMemcpyHostToDevice, s));
     return RKM_OK;
 }
 
@@ -312,7 +374,7 @@ rkm_status prep_rows(rkm_ctx* c, const PathShape& ps, const float* X, int64_t ro
     TRY(c->ensure(bnhat, rows, &out->nhat));
     TRY(c->ensure(bdel, rows, &out->del));
     launch_prep_rows(X, rows, ld, d, out->e, out->q, dq, out->n2, out->nrm, out->nhat, out->del, ps.tc,
-                     &c->st->grid_u, s);
+                     &c->st->off_grid, s);
     return RKM_OK;
 }
 
@@ -378,86 +440,131 @@ ItemBufs query_bufs(rkm_ctx* c) {
                     c->q_thmax, c->q_tdel};
 }
 
+// Threshold pass of one problem, split so that a batch can put many problems into one
+// launch of the tensor-core kernel: prepare (user pack, candidate buffers, arguments),
+// launch the product, then exact rescoring.  None of these waits for the device.
+struct ThrPlan {
+    ThresholdArgs a;
+    void* apack;
+    int64_t n_pad;
+    Cand* cand;
+    int* cand_cnt;
+    unsigned* lfin;
+    unsigned long long* keys;
+    int* kid;
+    int nseg, cap;
+};
+
+rkm_status threshold_prepare(rkm_ctx* c, const PathShape& ps, const float* U, int64_t n, int64_t ldu, int d, int k,
+                             const RowPrep& up, const ItemSide& it, ThrPlan* pl, cudaStream_t s) {
+    pl->n_pad = round_up(std::max<int64_t>(n, 1), BU);
+    {
+        Phase ph(c, s, RKM_PHASE_PREP);
+        TRY(pack(c, ps, U, n, ldu, d, nullptr, pl->n_pad, c->u_pack, &pl->apack, s));
+    }
+    pl->cap = c->cand_cap;
+    pl->nseg = ps.tc ? 2 : 1;
+    TRY(c->ensure(c->cand, n * (int64_t)pl->nseg * pl->cap, &pl->cand));
+    TRY(c->ensure(c->cand_cnt, n * (int64_t)pl->nseg, &pl->cand_cnt));
+    TRY(c->ensure(c->lfin, n, &pl->lfin));
+    TRY(c->ensure(c->keys, n * (int64_t)pl->nseg * pl->cap, &pl->keys));
+    TRY(c->ensure(c->kid, n * (int64_t)pl->nseg * pl->cap, &pl->kid));
+    CUDA_TRY(cudaMemsetAsync(pl->lfin, 0, n * sizeof(unsigned), s));
+    CUDA_TRY(cudaMemsetAsync(pl->cand_cnt, 0, n * pl->nseg * sizeof(int), s));
+    ThresholdArgs& a = pl->a;
+    a = ThresholdArgs{};
+    a.A = pl->apack;
+    a.B = it.pack;
+    a.n = n;
+    a.m = it.m;
+    a.dp = ps.dp;
+    a.k = k;
+    a.cap = pl->cap;
+    a.unrm = up.nrm;
+    a.unhat = up.nhat;
+    a.udel = up.del;
+    a.tmax = it.tmax;
+    a.thmax = it.thmax;
+    a.tdel = it.tdel;
+    a.cacc = ps.cacc;
+    a.eabs = ps.eabs;
+    a.cand = pl->cand;
+    a.cand_cnt = pl->cand_cnt;
+    a.lfin_key = pl->lfin;
+    a.nseg = pl->nseg;
+    a.st = c->st;
+    a.num_sms = c->num_sms;
+    return RKM_OK;
+}
+
+rkm_status threshold_descriptor(const PathShape& ps, const ThrPlan& pl, const ItemSide& it, TcInstance* out) {
+    TmapPair tm;
+    TRY(make_tmaps(pl.apack, pl.n_pad, it.pack, it.m_pad, ps.dp, BI_TC, &tm));
+    out->tmA = tm.a;
+    out->tmB = tm.b;
+    out->a = pl.a;
+    out->unit_begin = 0;
+    return RKM_OK;
+}
+
+rkm_status threshold_launch_one(rkm_ctx* c, const PathShape& ps, const ThrPlan& pl, const ItemSide& it,
+                                cudaStream_t s) {
+    Phase ph(c, s, RKM_PHASE_THRESHOLD);
+    c->stats.threshold_launches++;
+    if (ps.tc) {
+        TcInstance* hi;
+        TcInstance* di;
+        TRY(c->instances(1, &hi, &di));
+        TRY(threshold_descriptor(ps, pl, it, hi));
+        CUDA_TRY(cudaMemcpyAsync(di, hi, sizeof(TcInstance), cudaMemcpyHostToDevice, s));
+        launch_threshold_tc(di, 1, (pl.a.n + BU - 1) / BU, pl.a.k, ps.dp, c->num_sms, s);
+    } else {
+        launch_threshold_simt(pl.a, s);
+    }
+    return RKM_OK;
+}
+
+void threshold_exact(rkm_ctx* c, const float* U, int64_t ldu, const float* P, int64_t ldp, int d,
+                     const RowPrep& up, const ItemSide& it, const ThrPlan& pl, double* tau, int* tid, int* topk,
+                     cudaStream_t s) {
+    Phase ph(c, s, RKM_PHASE_EXACT);
+    ExactData x{U, ldu, up.e, up.q, P, ldp, it.rp.e, it.rp.q, d, (int)round_up(d, 8), &c->st->off_grid};
+    launch_exact_tau(x, pl.cand, pl.cand_cnt, pl.lfin, pl.cap, pl.nseg, it.perm, pl.a.n, pl.a.k, pl.keys, pl.kid,
+                     tau, tid, topk, c->st, s);
+}
+
+// Grow the candidate capacity after an overflow; false when it cannot grow any more.
+rkm_status grow_candidates(rkm_ctx* c, const PathShape& ps, int64_t n, int64_t m, int attempt) {
+    const int cap = c->cand_cap;
+    if (cap >= m || attempt >= 3)
+        return fail(RKM_EOVERFLOW, "candidate capacity %d overflowed after %d retries", cap, attempt);
+    const int64_t next = std::min<int64_t>(m, (int64_t)cap * 4);
+    if ((double)n * next * 20.0 * (ps.tc ? 2 : 1) > 64e9)
+        return fail(RKM_EOVERFLOW, "candidate lists need more than 64 GB (n=%lld, cap=%lld)", (long long)n,
+                    (long long)next);
+    c->cand_cap = (int)round_up(next, 32);
+    c->stats.retries++;
+    return RKM_OK;
+}
+
 rkm_status thresholds_core(rkm_ctx* c, const PathShape& ps, const float* U, int64_t n, int64_t ldu,
                            const float* P, int64_t ldp, int d, int k, const RowPrep& up, const ItemSide& it,
                            double* tau, int* tid, int* topk, cudaStream_t s) {
-    const int64_t n_pad = round_up(std::max<int64_t>(n, 1), BU);
-    void* apack;
-    {
-        Phase ph(c, s, RKM_PHASE_PREP);
-        TRY(pack(c, ps, U, n, ldu, d, nullptr, n_pad, c->u_pack, &apack, s));
-    }
-    int cap = c->cand_cap;
     for (int attempt = 0;; ++attempt) {
-        const int nseg = ps.tc ? 2 : 1;
-        Cand* cand;
-        int *cand_cnt, *kid;
-        unsigned* lfin;
-        unsigned long long* keys;
-        TRY(c->ensure(c->cand, n * (int64_t)nseg * cap, &cand));
-        TRY(c->ensure(c->cand_cnt, n * (int64_t)nseg, &cand_cnt));
-        TRY(c->ensure(c->lfin, n, &lfin));
-        TRY(c->ensure(c->keys, n * (int64_t)nseg * cap, &keys));
-        TRY(c->ensure(c->kid, n * (int64_t)nseg * cap, &kid));
-        CUDA_TRY(cudaMemsetAsync(lfin, 0, n * sizeof(unsigned), s));
-        CUDA_TRY(cudaMemsetAsync(cand_cnt, 0, n * nseg * sizeof(int), s));
-        ThresholdArgs a{};
-        a.A = apack;
-        a.B = it.pack;
-        a.n = n;
-        a.m = it.m;
-        a.dp = ps.dp;
-        a.k = k;
-        a.cap = cap;
-        a.unrm = up.nrm;
-        a.unhat = up.nhat;
-        a.udel = up.del;
-        a.tmax = it.tmax;
-        a.thmax = it.thmax;
-        a.tdel = it.tdel;
-        a.cacc = ps.cacc;
-        a.eabs = ps.eabs;
-        a.cand = cand;
-        a.cand_cnt = cand_cnt;
-        a.lfin_key = lfin;
-        a.nseg = nseg;
-        a.st = c->st;
-        a.num_sms = c->num_sms;
-        {
-            Phase ph(c, s, RKM_PHASE_THRESHOLD);
-            c->stats.threshold_launches++;
-            if (ps.tc) {
-                TmapPair tm;
-                TRY(make_tmaps(apack, n_pad, it.pack, it.m_pad, ps.dp, BI_TC, &tm));
-                launch_threshold_tc(a, &tm.a, &tm.b, s);
-            } else {
-                launch_threshold_simt(a, s);
-            }
-        }
-        {
-            Phase ph(c, s, RKM_PHASE_EXACT);
-            ExactData x{U, ldu, up.e, up.q, P, ldp, it.rp.e, it.rp.q, d, (int)round_up(d, 8), &c->st->grid_u};
-            launch_exact_tau(x, cand, cand_cnt, lfin, cap, nseg, it.perm, n, k, keys, kid, tau, tid, topk, c->st,
-                             s);
-        }
+        ThrPlan pl;
+        TRY(threshold_prepare(c, ps, U, n, ldu, d, k, up, it, &pl, s));
+        TRY(threshold_launch_one(c, ps, pl, it, s));
+        threshold_exact(c, U, ldu, P, ldp, d, up, it, pl, tau, tid, topk, s);
         TRY(read_status(c, s));
         if (!c->st_host->cand_overflow) break;
-        if (cap >= it.m || attempt >= 3)
-            return fail(RKM_EOVERFLOW, "candidate capacity %d overflowed after %d retries", cap, attempt);
-        const int64_t next = std::min<int64_t>(it.m, (int64_t)cap * 4);
-        if ((double)n * next * 20.0 * (ps.tc ? 2 : 1) > 64e9)
-            return fail(RKM_EOVERFLOW, "candidate lists need more than 64 GB (n=%lld, cap=%lld)",
-                        (long long)n, (long long)next);
-        cap = (int)round_up(next, 32);
-        c->cand_cap = cap;
-        c->stats.retries++;
+        TRY(grow_candidates(c, ps, n, it.m, attempt));
         CUDA_TRY(cudaMemsetAsync(&c->st->cand_overflow, 0, sizeof(unsigned), s));
         CUDA_TRY(cudaMemsetAsync(&c->st->internal_error, 0, sizeof(unsigned), s));
         CUDA_TRY(cudaMemsetAsync(&c->st->cand_total, 0, sizeof(unsigned long long), s));
     }
     if (c->st_host->internal_error) return fail(RKM_EINTERNAL, "threshold pass: fewer than k candidates");
     c->stats.candidates = c->st_host->cand_total;
-    c->stats.exact_integer_path = c->st_host->grid_u ? 1 : 0;
+    c->stats.exact_integer_path = c->st_host->off_grid ? 0 : 1;
     return RKM_OK;
 }
 
@@ -500,7 +607,7 @@ rkm_status count_stage(rkm_ctx* c, const PathShape& ps, int64_t n, const UserOrd
     unsigned* unit_off;
     TRY(c->ensure(c->nprefix, std::max<int64_t>(it.tiles, 1), &nprefix));
     TRY(c->ensure(c->unit_off, it.tiles + 2, &unit_off));
-    const int group = 32;  // user tiles per work unit (4096 users against one item tile)
+    const int group = c->count_group;  // user tiles per work unit
     Phase ph_count(c, s, RKM_PHASE_COUNT);
     launch_build_units(it.tmax, uo.ucum, t_begin, t_end, t_end_from_dev ? &c->st->t_end : nullptr, BU, group,
                        nprefix, unit_off, c->st, s);
@@ -590,6 +697,9 @@ void rkm_default_opts(rkm_opts* o) {
     o->cand_capacity = 0;
     o->band_capacity = 0;
     o->filter = 1;
+    o->profile = 0;
+    o->autotune = 0;
+    o->tune_cache = nullptr;
 }
 
 const char* rkm_last_error(void) { return g_err.c_str(); }
@@ -617,6 +727,8 @@ rkm_status rkm_create(rkm_ctx** out, const rkm_opts* opts, int device) {
     rkm_ctx* c = new rkm_ctx();
     c->device = device;
     c->opts = o;
+    if (o.tune_cache) c->tune_cache = o.tune_cache;
+    c->opts.tune_cache = nullptr;
     c->num_sms = prop.multiProcessorCount;
     cudaError_t e = cudaMalloc(&c->st, sizeof(DevStatus));
     if (e == cudaSuccess) e = cudaMallocHost(&c->st_host, sizeof(DevStatus));
@@ -633,6 +745,8 @@ void rkm_destroy(rkm_ctx* c) {
     if (!c) return;
     cudaSetDevice(c->device);
     cudaDeviceSynchronize();
+    for (rkm_ctx* sc : c->sub) rkm_destroy(sc);
+    c->sub.clear();
     c->free_all();
     if (c->st) cudaFree(c->st);
     if (c->st_host) cudaFreeHost(c->st_host);
@@ -673,64 +787,94 @@ rkm_status rkm_thresholds(rkm_ctx* c, const float* U, int64_t n, int64_t ldu, co
     return RKM_OK;
 }
 
+// Counting pass of one problem, split like the threshold pass: prepare (user ratios, their
+// bucket order, packs and records), then enqueue one attempt (stages, band rescoring, top-N)
+// without waiting for the device.
+struct CountPlan {
+    UserOrder uo;
+    ExactData x;
+    int* cnt;
+};
+
+rkm_status count_prepare(rkm_ctx* c, const PathShape& ps, const float* U, int64_t n, int64_t ldu, const float* P,
+                         int64_t ldp, int d, const RowPrep& up, const ItemSide& it, const double* tau,
+                         const int32_t* tid, CountPlan* cp, cudaStream_t s) {
+    {
+        Phase ph(c, s, RKM_PHASE_BOUNDS);
+        TRY(order_users(c, ps, U, n, ldu, d, up, tau, tid, UserBufs{c->uperm, c->ucum, c->us_pack, c->us_meta},
+                        &cp->uo, s));
+    }
+    cp->x = ExactData{U, ldu, up.e, up.q, P, ldp, it.rp.e, it.rp.q, d, (int)round_up(d, 8), &c->st->off_grid};
+    TRY(c->ensure(c->cnt_s, it.m, &cp->cnt));
+    return RKM_OK;
+}
+
+rkm_status count_enqueue(rkm_ctx* c, const PathShape& ps, int64_t n, const ItemSide& it, const CountPlan& cp,
+                         const double* tau, const int32_t* tid, int N, int32_t* scores, int32_t* ids,
+                         int32_t* top_scores, bool filter, cudaStream_t s) {
+    const UserOrder& uo = cp.uo;
+    const ExactData& x = cp.x;
+    int* cnt = cp.cnt;
+    int2* band;
+    TRY(ensure_band(c, &band));
+    CUDA_TRY(cudaMemsetAsync(cnt, 0, it.m * sizeof(int), s));
+    CUDA_TRY(cudaMemsetAsync(&c->st->band_count, 0, 2 * sizeof(unsigned), s));  // band_count, band_done
+    const int tiles = (int)it.tiles;
+    if (!filter) {
+        TRY(count_stage(c, ps, n, uo, it, false, 0, tiles, false, x, tau, tid, cnt, band, s));
+        TRY(band_stage(c, it, false, x, tau, tid, cnt, band, s));
+        Phase ph(c, s, RKM_PHASE_TOPN);
+        if (scores) scatter_i32(cnt, it.perm, it.m, scores, s);
+        if (ids) launch_topn(cnt, it.perm, it.m, nullptr, N, ids, top_scores, c->st, s);
+        return RKM_OK;
+    }
+    // First stage: enough leading tiles (largest norms, so largest bounds) to hold N items
+    // and a few thousand more; its N-th score is an exact lower bound of the final one.
+    const int64_t c0 = std::max<int64_t>(4 * (int64_t)N, c->stage1_items);
+    const int t0 = (int)std::min<int64_t>(tiles, (c0 + ps.item_tile - 1) / ps.item_tile);
+    TRY(count_stage(c, ps, n, uo, it, false, 0, t0, false, x, tau, tid, cnt, band, s));
+    TRY(band_stage(c, it, false, x, tau, tid, cnt, band, s));
+    int *tids_c0, *tsc_c0;
+    TRY(c->ensure(c->top_ids, N, &tids_c0));
+    TRY(c->ensure(c->top_sc, N, &tsc_c0));
+    const int64_t m0 = std::min<int64_t>(it.m, (int64_t)t0 * ps.item_tile);
+    if (t0 < tiles) {
+        {
+            Phase ph(c, s, RKM_PHASE_TOPN);
+            launch_topn(cnt, it.perm, m0, nullptr, N, tids_c0, tsc_c0, c->st, s);
+            launch_filter_cut(tsc_c0, N, it.tmax, uo.ucum, it.tiles, t0, ps.item_tile, it.m, c->st, s);
+        }
+        TRY(count_stage(c, ps, n, uo, it, false, t0, 0, true, x, tau, tid, cnt, band, s));
+        TRY(band_stage(c, it, false, x, tau, tid, cnt, band, s));
+        Phase ph(c, s, RKM_PHASE_TOPN);
+        launch_topn(cnt, it.perm, it.m, &c->st->m_counted, N, ids, top_scores, c->st, s);
+    } else {
+        Phase ph(c, s, RKM_PHASE_TOPN);
+        launch_topn(cnt, it.perm, it.m, nullptr, N, ids, top_scores, c->st, s);
+    }
+    return RKM_OK;
+}
+
+// Grow the band queue after an overflow.
+rkm_status grow_band(rkm_ctx* c, int attempt) {
+    if (attempt >= 3) return fail(RKM_EOVERFLOW, "band queue (%lld pairs) overflowed", (long long)c->band_cap);
+    c->band_cap = std::min<int64_t>((int64_t)UINT32_MAX - 1,
+                                    std::max<int64_t>(c->band_cap * 2, (int64_t)c->st_host->band_count + 1024));
+    c->stats.retries++;
+    return RKM_OK;
+}
+
 static rkm_status scores_impl(rkm_ctx* c, const PathShape& ps, const float* U, int64_t n, int64_t ldu,
                               const float* P, int64_t ldp, int d, const RowPrep& up, const ItemSide& it,
                               const double* tau, const int32_t* tid, int N, int32_t* scores, int32_t* ids,
                               int32_t* top_scores, bool filter, cudaStream_t s) {
-    UserOrder uo;
-    {
-        Phase ph(c, s, RKM_PHASE_BOUNDS);
-        TRY(order_users(c, ps, U, n, ldu, d, up, tau, tid,
-                        UserBufs{c->uperm, c->ucum, c->us_pack, c->us_meta},
-                        &uo, s));
-    }
-    ExactData x{U, ldu, up.e, up.q, P, ldp, it.rp.e, it.rp.q, d, (int)round_up(d, 8), &c->st->grid_u};
-    int* cnt;
-    TRY(c->ensure(c->cnt_s, it.m, &cnt));
+    CountPlan cp;
+    TRY(count_prepare(c, ps, U, n, ldu, P, ldp, d, up, it, tau, tid, &cp, s));
     for (int attempt = 0;; ++attempt) {
-        int2* band;
-        TRY(ensure_band(c, &band));
-        CUDA_TRY(cudaMemsetAsync(cnt, 0, it.m * sizeof(int), s));
-        CUDA_TRY(cudaMemsetAsync(&c->st->band_count, 0, 2 * sizeof(unsigned), s));  // band_count, band_done
-        const int tiles = (int)it.tiles;
-        if (!filter) {
-            TRY(count_stage(c, ps, n, uo, it, false, 0, tiles, false, x, tau, tid, cnt, band, s));
-            TRY(band_stage(c, it, false, x, tau, tid, cnt, band, s));
-            Phase ph(c, s, RKM_PHASE_TOPN);
-            if (scores) scatter_i32(cnt, it.perm, it.m, scores, s);
-            if (ids) launch_topn(cnt, it.perm, it.m, nullptr, N, ids, top_scores, c->st, s);
-        } else {
-            // First stage: enough leading tiles (largest norms, so largest bounds) to hold
-            // N items and a few thousand more; its N-th score is an exact lower bound.
-            int64_t c0 = std::max<int64_t>(4 * (int64_t)N, 8192);
-            int t0 = (int)std::min<int64_t>(tiles, (c0 + ps.item_tile - 1) / ps.item_tile);
-            TRY(count_stage(c, ps, n, uo, it, false, 0, t0, false, x, tau, tid, cnt, band, s));
-            TRY(band_stage(c, it, false, x, tau, tid, cnt, band, s));
-            int *tids_c0, *tsc_c0;
-            TRY(c->ensure(c->top_ids, N, &tids_c0));
-            TRY(c->ensure(c->top_sc, N, &tsc_c0));
-            const int64_t m0 = std::min<int64_t>(it.m, (int64_t)t0 * ps.item_tile);
-            if (t0 < tiles) {
-                {
-                    Phase ph(c, s, RKM_PHASE_TOPN);
-                    launch_topn(cnt, it.perm, m0, nullptr, N, tids_c0, tsc_c0, c->st, s);
-                    launch_filter_cut(tsc_c0, N, it.tmax, uo.ucum, it.tiles, t0, ps.item_tile, it.m, c->st, s);
-                }
-                TRY(count_stage(c, ps, n, uo, it, false, t0, 0, true, x, tau, tid, cnt, band, s));
-                TRY(band_stage(c, it, false, x, tau, tid, cnt, band, s));
-                Phase ph(c, s, RKM_PHASE_TOPN);
-                launch_topn(cnt, it.perm, it.m, &c->st->m_counted, N, ids, top_scores, c->st, s);
-            } else {
-                Phase ph(c, s, RKM_PHASE_TOPN);
-                launch_topn(cnt, it.perm, it.m, nullptr, N, ids, top_scores, c->st, s);
-            }
-        }
+        TRY(count_enqueue(c, ps, n, it, cp, tau, tid, N, scores, ids, top_scores, filter, s));
         TRY(read_status(c, s));
         if (!c->st_host->band_overflow) break;
-        if (attempt >= 3) return fail(RKM_EOVERFLOW, "band queue (%lld pairs) overflowed", (long long)c->band_cap);
-        c->band_cap = std::min<int64_t>((int64_t)UINT32_MAX - 1,
-                                        std::max<int64_t>(c->band_cap * 2, (int64_t)c->st_host->band_count + 1024));
-        c->stats.retries++;
+        TRY(grow_band(c, attempt));
         CUDA_TRY(cudaMemsetAsync(&c->st->band_overflow, 0, sizeof(unsigned), s));
     }
     if (c->st_host->internal_error) return fail(RKM_EINTERNAL, "counting pass: device consistency check failed");
@@ -769,7 +913,7 @@ rkm_status rkm_scores(rkm_ctx* c, const float* U, int64_t n, int64_t ldu, const 
     }
     TRY(scores_impl(c, ps, U, n, ldu, P, ldp, d, up, it, tau, tid, 0, scores, nullptr, nullptr, false, s));
     c->stats.pairs_total = (uint64_t)n * (uint64_t)m;
-    c->stats.exact_integer_path = c->st_host->grid_u ? 1 : 0;
+    c->stats.exact_integer_path = c->st_host->off_grid ? 0 : 1;
     c->stats.last_ms = now_ms() - t0;
     return RKM_OK;
 }
@@ -902,7 +1046,7 @@ rkm_status rkm_resident_set(rkm_ctx* c, const float* U, int64_t n, int64_t ldu, 
                     UserBufs{c->res_uperm, c->res_ucum, c->res_pack, c->res_meta},
                     &uo, s));
     TRY(read_status(c, s));
-    c->res_grid = c->st_host->grid_u;
+    c->res_off_grid = c->st_host->off_grid;
     c->res_n = n;
     c->res_d = d;
     c->resident = true;
@@ -929,7 +1073,7 @@ rkm_status rkm_query_new_items(rkm_ctx* c, const float* Q, int64_t q, int64_t ld
     const PathShape ps = path_shape(c->opts.precision, d);
     init_caps(c, std::max<int64_t>(n / 64, q * 64), 1);
     TRY(begin_call(c, s));
-    CUDA_TRY(cudaMemcpyAsync(&c->st->grid_u, &c->res_grid, sizeof(unsigned), cudaMemcpyHostToDevice, s));
+    if (c->res_off_grid) CUDA_TRY(cudaMemsetAsync(&c->st->off_grid, 1, 1, s));
     ItemSide it;
     {
         Phase ph(c, s, RKM_PHASE_PREP);
@@ -939,7 +1083,7 @@ rkm_status rkm_query_new_items(rkm_ctx* c, const float* Q, int64_t q, int64_t ld
                  static_cast<UserMeta*>(c->res_meta.p)};
     ExactData x{static_cast<const float*>(c->res_U.p), d, static_cast<const int*>(c->res_e.p),
                 static_cast<const int16_t*>(c->res_q.p), Q, ldq, it.rp.e, it.rp.q, d, (int)round_up(d, 8),
-                &c->st->grid_u};
+                &c->st->off_grid};
     int* cnt;
     TRY(c->ensure(c->q_cnt, q, &cnt));
     for (int attempt = 0;; ++attempt) {
@@ -964,9 +1108,331 @@ rkm_status rkm_query_new_items(rkm_ctx* c, const float* Q, int64_t q, int64_t ld
     c->stats.pairs_total = (uint64_t)n * (uint64_t)q;
     c->stats.pairs_evaluated = c->st_host->pairs_evaluated;
     c->stats.band_pairs = c->st_host->band_count;
-    c->stats.exact_integer_path = c->st_host->grid_u ? 1 : 0;
+    c->stats.exact_integer_path = c->st_host->off_grid ? 0 : 1;
     c->stats.last_ms = now_ms() - t0;
     return RKM_OK;
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------- batches
+
+namespace {
+
+rkm_ctx* make_sub(const rkm_ctx* parent) {
+    rkm_ctx* c = new rkm_ctx();
+    c->device = parent->device;
+    c->opts = parent->opts;
+    c->opts.profile = 0;
+    c->num_sms = parent->num_sms;
+    if (cudaMalloc(&c->st, sizeof(DevStatus)) != cudaSuccess ||
+        cudaMallocHost(&c->st_host, sizeof(DevStatus)) != cudaSuccess) {
+        cudaGetLastError();
+        if (c->st) cudaFree(c->st);
+        delete c;
+        return nullptr;
+    }
+    return c;
+}
+
+struct InstWork {
+    PathShape ps;
+    RowPrep up;
+    ItemSide it;
+    ThrPlan pl;
+    CountPlan cp;
+    double* tau;
+    int* tid;
+};
+
+int64_t instance_cost(const rkm_instance& I, const PathShape& ps) {
+    return ((I.n + BU - 1) / BU) * ((I.m + BI_TC - 1) / BI_TC) * (ps.dp / 64);
+}
+
+// Every kernel of a batch, in order, on one stream, without host waits (so that the sequence
+// can be captured into a graph): per instance prep and threshold arguments; one threshold
+// launch over all instances (largest first); per instance exact rescoring, counting, top-N.
+rkm_status batch_enqueue(rkm_ctx* c, const rkm_instance* inst, int count, cudaStream_t s) {
+    std::vector<InstWork> w(count);
+    for (int i = 0; i < count; ++i) {
+        rkm_ctx* sc = c->sub[i];
+        const rkm_instance& I = inst[i];
+        InstWork& x = w[i];
+        x.ps = path_shape(c->opts.precision, I.d);
+        init_caps(sc, I.n, I.k);
+        TRY(begin_call(sc, s));
+        TRY(prep_rows(sc, x.ps, I.U, I.n, I.ldu, I.d, sc->u_e, sc->u_q, sc->u_n2, sc->u_nrm, sc->u_nhat, sc->u_del,
+                      &x.up, s));
+        TRY(prep_items(sc, x.ps, I.P, I.m, I.ldp, I.d, catalogue_bufs(sc), &x.it, s));
+        TRY(threshold_prepare(sc, x.ps, I.U, I.n, I.ldu, I.d, I.k, x.up, x.it, &x.pl, s));
+        TRY(sc->ensure(sc->tau_tmp, I.n, &x.tau));
+        TRY(sc->ensure(sc->tid_tmp, I.n, &x.tid));
+    }
+    if (w[0].ps.tc) {
+        std::vector<int> order(count);
+        for (int i = 0; i < count; ++i) order[i] = i;
+        std::stable_sort(order.begin(), order.end(), [&](int x, int y) {
+            return instance_cost(inst[x], w[x].ps) > instance_cost(inst[y], w[y].ps);
+        });
+        if (c->batch_host_cap < count) {
+            if (c->batch_host) cudaFreeHost(c->batch_host);
+            c->batch_host = nullptr;
+            c->batch_host_cap = 0;
+            CUDA_TRY(cudaMallocHost(&c->batch_host, (size_t)count * sizeof(TcInstance)));
+            c->batch_host_cap = count;
+        }
+        TcInstance* dev;
+        TRY(c->ensure(c->batch_dev, count, &dev));
+        long long units = 0;
+        int kheap = 1, max_dp = 64;
+        for (int j = 0; j < count; ++j) {
+            const int i = order[j];
+            TRY(threshold_descriptor(w[i].ps, w[i].pl, w[i].it, &c->batch_host[j]));
+            c->batch_host[j].unit_begin = units;
+            units += (inst[i].n + BU - 1) / BU;
+            kheap = std::max(kheap, inst[i].k);
+            max_dp = std::max(max_dp, w[i].ps.dp);
+        }
+        CUDA_TRY(cudaMemcpyAsync(dev, c->batch_host, (size_t)count * sizeof(TcInstance), cudaMemcpyHostToDevice, s));
+        launch_threshold_tc(dev, count, units, kheap, max_dp, c->num_sms, s);
+    } else {
+        for (int i = 0; i < count; ++i) launch_threshold_simt(w[i].pl.a, s);
+    }
+    for (int i = 0; i < count; ++i) {
+        rkm_ctx* sc = c->sub[i];
+        const rkm_instance& I = inst[i];
+        InstWork& x = w[i];
+        threshold_exact(sc, I.U, I.ldu, I.P, I.ldp, I.d, x.up, x.it, x.pl, x.tau, x.tid, nullptr, s);
+        TRY(count_prepare(sc, x.ps, I.U, I.n, I.ldu, I.P, I.ldp, I.d, x.up, x.it, x.tau, x.tid, &x.cp, s));
+        TRY(count_enqueue(sc, x.ps, I.n, x.it, x.cp, x.tau, x.tid, I.N, nullptr, I.ids, I.top_scores,
+                          c->opts.filter != 0, s));
+    }
+    return RKM_OK;
+}
+
+bool same_layout(const std::vector<rkm_instance>& key, const rkm_instance* inst, int count) {
+    if ((int)key.size() != count) return false;
+    for (int i = 0; i < count; ++i) {
+        const rkm_instance& a = key[i];
+        const rkm_instance& b = inst[i];
+        if (a.U != b.U || a.n != b.n || a.ldu != b.ldu || a.P != b.P || a.m != b.m || a.ldp != b.ldp ||
+            a.d != b.d || a.k != b.k || a.N != b.N || a.ids != b.ids || a.top_scores != b.top_scores)
+            return false;
+    }
+    return true;
+}
+
+void drop_graph(rkm_ctx* c) {
+    if (c->graph_exec) cudaGraphExecDestroy(c->graph_exec);
+    if (c->graph) cudaGraphDestroy(c->graph);
+    c->graph_exec = nullptr;
+    c->graph = nullptr;
+    c->graph_key.clear();
+}
+
+// ---- autotuner: counting work-unit size and first-stage size per size bucket
+
+struct TuneChoice {
+    int group;
+    int64_t stage1;
+};
+
+std::string tune_bucket(const rkm_instance& I, int prec) {
+    auto lg = [](int64_t x) { int b = 0; while ((int64_t(1) << (b + 1)) <= x) ++b; return b; };
+    char buf[96];
+    snprintf(buf, sizeof buf, "p%d_d%d_k%d_n%d_m%d", prec, I.d, I.k, lg(I.n) / 2, lg(I.m) / 2);
+    return buf;
+}
+
+void load_tune_table(rkm_ctx* c) {
+    if (c->tune_loaded) return;
+    c->tune_loaded = true;
+    if (c->tune_cache.empty()) return;
+    std::ifstream f(c->tune_cache);
+    std::string key;
+    int g;
+    long long s1;
+    while (f >> key >> g >> s1) c->tune[key] = {g, (int64_t)s1};
+}
+
+void save_tune_table(const rkm_ctx* c) {
+    if (c->tune_cache.empty()) return;
+    std::ofstream f(c->tune_cache);
+    for (const auto& kv : c->tune) f << kv.first << " " << kv.second.first << " " << kv.second.second << "\n";
+}
+
+// Time rkm_topn on this instance for each candidate and keep the fastest.
+rkm_status tune_instance(rkm_ctx* sc, const rkm_instance& I, cudaStream_t s, TuneChoice* best) {
+    static const int groups[] = {8, 16, 32};
+    static const int64_t stages[] = {4096, 16384};
+    cudaEvent_t e0, e1;
+    CUDA_TRY(cudaEventCreate(&e0));
+    CUDA_TRY(cudaEventCreate(&e1));
+    float best_ms = 1e30f;
+    *best = TuneChoice{32, 8192};
+    for (int g : groups) {
+        for (int64_t st1 : stages) {
+            sc->count_group = g;
+            sc->stage1_items = st1;
+            float ms = 0.f;
+            for (int rep = 0; rep < 2; ++rep) {  // the first run may grow the workspace
+                cudaEventRecord(e0, s);
+                const rkm_status r = rkm_topn(sc, I.U, I.n, I.ldu, I.P, I.m, I.ldp, I.d, I.k, I.N, I.ids,
+                                              I.top_scores, nullptr, nullptr, s);
+                cudaEventRecord(e1, s);
+                if (r != RKM_OK) {
+                    cudaEventDestroy(e0);
+                    cudaEventDestroy(e1);
+                    return r;
+                }
+                cudaEventSynchronize(e1);
+                cudaEventElapsedTime(&ms, e0, e1);
+            }
+            if (ms < best_ms) {
+                best_ms = ms;
+                *best = TuneChoice{g, st1};
+            }
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    return RKM_OK;
+}
+
+}  // namespace
+
+extern "C" rkm_status rkm_topn_batch(rkm_ctx* c, const rkm_instance* inst, int count, void* stream) {
+    if (!c) return fail(RKM_EINVAL, "null context");
+    if (!inst || count < 1 || count > 4096) return fail(RKM_EINVAL, "count must be in [1, 4096]");
+    const double t0 = now_ms();
+    for (int i = 0; i < count; ++i) {
+        const rkm_instance& I = inst[i];
+        TRY(check_common(c, I.d));
+        TRY(check_matrix(I.U, I.n, I.ldu, I.d, "U"));
+        TRY(check_matrix(I.P, I.m, I.ldp, I.d, "P"));
+        if (I.n < 1) return fail(RKM_EINVAL, "instance %d: n must be >= 1", i);
+        if (I.k < 1 || I.k > I.m || I.k > c->opts.k_max) return fail(RKM_EINVAL, "instance %d: bad k", i);
+        if (I.N < 1 || I.N > I.m || I.N > NMAX_TOPN) return fail(RKM_EINVAL, "instance %d: bad N", i);
+        if (!I.ids || !I.top_scores) return fail(RKM_EINVAL, "instance %d: null outputs", i);
+        if (path_shape(c->opts.precision, I.d).tc != path_shape(c->opts.precision, inst[0].d).tc)
+            return fail(RKM_EINVAL, "instances must share one precision path");
+    }
+    reset_stats(c);
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    while ((int)c->sub.size() < count) {
+        rkm_ctx* sc = make_sub(c);
+        if (!sc) return fail(RKM_ENOMEM, "sub-context allocation failed");
+        c->sub.push_back(sc);
+    }
+    // Tunables per instance (autotuned or default).
+    load_tune_table(c);
+    bool tuned_any = false;
+    for (int i = 0; i < count; ++i) {
+        rkm_ctx* sc = c->sub[i];
+        const std::string key = tune_bucket(inst[i], (int)c->opts.precision);
+        auto f = c->tune.find(key);
+        if (f == c->tune.end() && c->opts.autotune) {
+            TuneChoice ch;
+            TRY(tune_instance(sc, inst[i], s, &ch));
+            c->tune[key] = {ch.group, ch.stage1};
+            tuned_any = true;
+            f = c->tune.find(key);
+        }
+        const int g = (f != c->tune.end()) ? f->second.first : 32;
+        const int64_t s1 = (f != c->tune.end()) ? f->second.second : 8192;
+        if (sc->count_group != g || sc->stage1_items != s1) drop_graph(c);
+        sc->count_group = g;
+        sc->stage1_items = s1;
+    }
+    if (tuned_any) save_tune_table(c);
+    if (!c->bstream) {
+        CUDA_TRY(cudaStreamCreateWithFlags(&c->bstream, cudaStreamNonBlocking));
+        CUDA_TRY(cudaEventCreateWithFlags(&c->bev_in, cudaEventDisableTiming));
+        CUDA_TRY(cudaEventCreateWithFlags(&c->bev_out, cudaEventDisableTiming));
+    }
+    // The batch runs on the internal stream after the caller's prior work.
+    CUDA_TRY(cudaEventRecord(c->bev_in, s));
+    CUDA_TRY(cudaStreamWaitEvent(c->bstream, c->bev_in, 0));
+    cudaStream_t caller = s;
+    s = c->bstream;
+    const unsigned long long l0 = g_launches.load();
+    const int okey = (int)c->opts.precision * 2 + (c->opts.filter ? 1 : 0);
+    const bool replay = c->graph_exec && c->graph_opts_key == okey && same_layout(c->graph_key, inst, count);
+    if (replay) {
+        CUDA_TRY(cudaGraphLaunch(c->graph_exec, s));
+    } else {
+        drop_graph(c);
+        TRY(batch_enqueue(c, inst, count, s));
+    }
+    for (int i = 0; i < count; ++i)
+        CUDA_TRY(cudaMemcpyAsync(c->sub[i]->st_host, c->sub[i]->st, sizeof(DevStatus), cudaMemcpyDeviceToHost, s));
+    CUDA_TRY(cudaStreamSynchronize(s));
+    CUDA_TRY(cudaGetLastError());
+    unsigned long long launches = replay ? c->graph_kernels : g_launches.load() - l0;
+    // Instances that overflowed a buffer (or failed a check) inside the batch are recomputed by
+    // the retrying single-instance path; their workspace may grow, so the graph is rebuilt.
+    bool redo = false;
+    for (int i = 0; i < count; ++i) {
+        const DevStatus& st = *c->sub[i]->st_host;
+        if (st.cand_overflow || st.band_overflow || st.internal_error || st.timeout) {
+            const rkm_instance& I = inst[i];
+            const unsigned long long l1 = g_launches.load();
+            TRY(rkm_topn(c->sub[i], I.U, I.n, I.ldu, I.P, I.m, I.ldp, I.d, I.k, I.N, I.ids, I.top_scores, nullptr,
+                         nullptr, s));
+            launches += g_launches.load() - l1;
+            c->stats.retries++;
+            redo = true;
+        }
+        c->stats.candidates += st.cand_total;
+        c->stats.band_pairs += st.band_count;
+        c->stats.pairs_evaluated += st.pairs_evaluated + (uint64_t)inst[i].n * (uint64_t)inst[i].m;
+        c->stats.pairs_total += 2ull * (uint64_t)inst[i].n * (uint64_t)inst[i].m;
+    }
+    if (redo) drop_graph(c);
+    if (!replay && !redo) {
+        // Capture the same sequence for the next call with this layout (buffers are in place,
+        // so nothing is allocated while capturing).
+        if (cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+            cudaGetLastError();
+            c->stats.kernel_launches = launches;
+            c->stats.last_ms = now_ms() - t0;
+            return RKM_OK;
+        }
+        const unsigned long long lc = g_launches.load();
+        const rkm_status r = batch_enqueue(c, inst, count, s);
+        cudaGraph_t g = nullptr;
+        const cudaError_t e = cudaStreamEndCapture(s, &g);
+        g_launches.fetch_sub(g_launches.load() - lc);  // nothing ran while capturing
+        if (r == RKM_OK && e == cudaSuccess && g) {
+            cudaGraphExec_t ex = nullptr;
+            if (cudaGraphInstantiate(&ex, g, 0) == cudaSuccess) {
+                c->graph = g;
+                c->graph_exec = ex;
+                c->graph_key.assign(inst, inst + count);
+                c->graph_opts_key = okey;
+                c->graph_kernels = 0;  // the kernel nodes of the graph
+                size_t nn = 0;
+                cudaGraphGetNodes(g, nullptr, &nn);
+                std::vector<cudaGraphNode_t> nodes(nn);
+                cudaGraphGetNodes(g, nodes.data(), &nn);
+                for (cudaGraphNode_t nd : nodes) {
+                    cudaGraphNodeType ty;
+                    if (cudaGraphNodeGetType(nd, &ty) == cudaSuccess && ty == cudaGraphNodeTypeKernel)
+                        ++c->graph_kernels;
+                }
+            } else {
+                cudaGetLastError();
+                cudaGraphDestroy(g);
+            }
+        } else {
+            cudaGetLastError();
+            if (g) cudaGraphDestroy(g);
+        }
+    }
+    c->stats.kernel_launches = launches;
+    c->stats.last_ms = now_ms() - t0;
+    // Later work on the caller's stream follows the batch.
+    CUDA_TRY(cudaEventRecord(c->bev_out, s));
+    CUDA_TRY(cudaStreamWaitEvent(caller, c->bev_out, 0));
+    return RKM_OK;
+}

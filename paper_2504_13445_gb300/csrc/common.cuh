@@ -22,8 +22,8 @@ struct DevStatus {
     unsigned int band_overflow;   // the band queue was full
     unsigned int internal_error;  // a consistency check failed (e.g. < k candidates)
     unsigned int timeout;         // a bounded wait gave up
-    unsigned int grid_u;          // 1 while every user row is on the 2^-12 grid
-    unsigned int grid_p;          // 1 while every item row is on the grid
+    unsigned int off_grid;        // set when a user or item row is not on the 2^-12 grid
+    unsigned int unused0;
     unsigned int band_count;      // pairs pushed to the band queue (may exceed capacity)
     unsigned int band_done;       // pairs of the queue already rescored
     unsigned int ticket;          // work ticket of the persistent counting kernel

@@ -69,7 +69,7 @@ __global__ void k_exact_tau(ExactData x, const Cand* __restrict__ cand, const in
                             int* __restrict__ topk, DevStatus* st) {
     const int lane = threadIdx.x & 31;
     const unsigned lt_mask = (1u << lane) - 1u;
-    const bool grid = *x.grid != 0u;
+    const bool grid = *x.off_grid == 0u;
     const int64_t warps = ((int64_t)gridDim.x * blockDim.x) >> 5;
     unsigned long long kept_total = 0;
     for (int64_t u = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; u < n; u += warps) {
@@ -142,7 +142,7 @@ __global__ void k_band_rescore(ExactData x, const int2* __restrict__ band, unsig
                                const int* __restrict__ item_perm, const double* __restrict__ tau,
                                const int* __restrict__ tid, bool new_items, int* __restrict__ counts,
                                DevStatus* st) {
-    const bool grid = *x.grid != 0u;
+    const bool grid = *x.off_grid == 0u;
     const unsigned begin = st->band_done;
     unsigned end = st->band_count;
     if (end > band_cap) end = band_cap;

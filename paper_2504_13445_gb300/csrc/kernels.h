@@ -1,6 +1,7 @@
 // Internal launchers of the reverse k-MIPS kernels (host side, not part of the C ABI).
 #pragma once
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -20,7 +21,8 @@ inline void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); 
 // ---- prep.cu (K1 prep, K4 bounds and the bucket sort) ------------------------------
 
 // Per row: exponent e (max|x| <= 2^e), integer grid codes q = x * 2^(12-e) (int16,
-// row stride dq), exact/upper-bound squared norm, ||x|| rounded up, grid flag.
+// row stride dq), exact/upper-bound squared norm, ||x|| rounded up; *grid_flag is set to 1
+// when a row is not on the grid.
 // Also ||x^|| and ||x^ - x|| (rounded up) of the operand x^ the product kernels see:
 // x^ = BF16 round-to-nearest of x when round_bf16, else x itself.
 void launch_prep_rows(const float* X, int64_t rows, int64_t ld, int d, int* ex, int16_t* q,
@@ -82,8 +84,20 @@ struct ThresholdArgs {
     int num_sms;
 };
 void launch_threshold_simt(const ThresholdArgs& a, cudaStream_t s);
-void launch_threshold_tc(const ThresholdArgs& a, const void* tmapA, const void* tmapB,
-                         cudaStream_t s);
+
+// One problem of the tensor-core threshold pass: its TMA descriptors (users, items), its
+// arguments, and the index of its first work unit (user tile) in the launch.
+struct __align__(64) TcInstance {
+    CUtensorMap tmA;
+    CUtensorMap tmB;
+    ThresholdArgs a;
+    long long unit_begin;
+};
+// Tensor-core threshold pass over `count` instances in one persistent launch.  inst: device
+// array; total_units = sum of the instances' user tiles; kheap = largest k; max_dp = largest
+// padded depth.
+void launch_threshold_tc(const TcInstance* inst, int count, long long total_units, int kheap, int max_dp,
+                         int num_sms, cudaStream_t s);
 
 // ---- exact rescoring (K3, K6, K8) ---------------------------------------------------
 
@@ -95,7 +109,7 @@ struct ExactData {
     const float* P; int64_t ldp;
     const int* ep; const int16_t* qp;
     int d, dq;
-    const unsigned* grid;  // device flag: nonzero = use the integer path
+    const unsigned* off_grid;  // device flag: zero = every row on the grid, use the integer path
 };
 
 // K3: exact tau_u, t_u and (optionally) S_k(u) from the candidate lists.

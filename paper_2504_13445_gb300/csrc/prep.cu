@@ -74,7 +74,7 @@ __global__ void k_prep_rows(const float* __restrict__ X, int64_t rows, int64_t l
                 n2 = ldexp((double)s2, 2 * e - 24);  // exact
             } else {
                 n2 = (double)d2;                     // an upper bound
-                atomicAnd(grid_flag, 0u);
+                atomicOr(grid_flag, 1u);
             }
             ex[row] = e;
             norm2[row] = n2;

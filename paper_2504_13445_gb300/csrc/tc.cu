@@ -106,9 +106,24 @@ __device__ __forceinline__ void teardown(TcBars* B, int warp) {
 
 // ---------------------------------------------------------------- K2
 
+// Instance of a work unit w (its global user-tile index): the last instance whose first unit
+// is <= w (instances are few; a binary search over their first units).
+__device__ __forceinline__ int unit_instance(const TcInstance* inst, int count, long long w) {
+    int lo = 0, hi = count;
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (inst[mid].unit_begin <= w) lo = mid; else hi = mid;
+    }
+    return lo;
+}
+
+// Threshold pass over one or many independent problems.  Work units are (instance, user
+// tile) pairs numbered consecutively across the instances; CTA b takes units b, b + grid, ...
+// A unit streams every item tile of its instance, so the caller orders the instances by
+// descending cost to balance the CTAs.
 __global__ void __launch_bounds__(TC_THREADS, 1)
-    k_threshold_tc(const ThresholdArgs a, const __grid_constant__ CUtensorMap tmA,
-                   const __grid_constant__ CUtensorMap tmB, const TcLayout L) {
+    k_threshold_tc(const TcInstance* __restrict__ inst, int count, long long total_units, int kheap,
+                   const TcLayout L) {
     extern __shared__ uint8_t smem_raw[];
     uint8_t* sm = align1024(smem_raw);
     uint8_t* sA = sm + L.res_off;
@@ -116,15 +131,12 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     float* heaps = reinterpret_cast<float*>(sm + L.aux_off);
     TcBars* B = reinterpret_cast<TcBars*>(sm + L.bar_off);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int KB = a.dp >> 6;
     const int S = L.slots;
-    const int64_t user_tiles = (a.n + BU - 1) / BU;
-    const int64_t item_tiles = (a.m + BI_TC - 1) / BI_TC;
     volatile int* abort = &B->abort;
     // Running bounds published per user row by each epilogue group: Lpub[h][row], tagged with
-    // the user tile (a bound of another user tile is never used).  Initialised before setup's
+    // the work unit (a bound of another unit is never used).  Initialised before setup's
     // barrier so that no group can read an uninitialised entry.
-    unsigned long long* Lpub = reinterpret_cast<unsigned long long*>(heaps + 2 * a.k * BU);
+    unsigned long long* Lpub = reinterpret_cast<unsigned long long*>(heaps + 2 * kheap * BU);
     if (warp >= 2) Lpub[threadIdx.x - 64] = 0xFFFFFFFF00000000ull;
 
     setup(B, S, warp);
@@ -132,29 +144,33 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
 
     if (warp == 0) {
         if (lane == 0) {
-            tma_prefetch_desc(&tmA);
-            tma_prefetch_desc(&tmB);
             int slot = 0;
             uint32_t ph = 0;
             int issued[MAX_SLOTS] = {0, 0, 0, 0};
             int res_loads = 0;
             bool ok = true;
-            for (int64_t ut = blockIdx.x; ut < user_tiles && ok; ut += gridDim.x) {
+            DevStatus* st = inst[0].a.st;
+            for (long long w = blockIdx.x; w < total_units && ok; w += gridDim.x) {
+                const TcInstance& I = inst[unit_instance(inst, count, w)];
+                st = I.a.st;
+                const int KB = I.a.dp >> 6;
+                const long long ut = w - I.unit_begin;
+                const int item_tiles = (int)((I.a.m + BI_TC - 1) / BI_TC);
                 const int rb = res_loads % L.nres, ru = res_loads / L.nres;
-                if (ru > 0 && !mbar_wait(&B->res_empty[rb], (ru - 1) & 1, abort, a.st)) break;
+                if (ru > 0 && !mbar_wait(&B->res_empty[rb], (ru - 1) & 1, abort, st)) break;
                 uint8_t* dst = sA + rb * L.res_bytes;
                 mbar_expect_tx(&B->res_full[rb], KB * KB_BYTES_U);
                 for (int kb = 0; kb < KB; ++kb)
-                    tma_load_2d(dst + kb * KB_BYTES_U, &tmA, &B->res_full[rb], kb * 64, (int)(ut * BU));
+                    tma_load_2d(dst + kb * KB_BYTES_U, &I.tmA, &B->res_full[rb], kb * 64, (int)(ut * BU));
                 ++res_loads;
-                for (int64_t it = 0; it < item_tiles && ok; ++it) {
+                for (int it = 0; it < item_tiles && ok; ++it) {
                     for (int kb = 0; kb < KB; ++kb) {
-                        if (!mbar_wait(&B->empty[slot], ph ^ 1u, abort, a.st)) {
+                        if (!mbar_wait(&B->empty[slot], ph ^ 1u, abort, st)) {
                             ok = false;
                             break;
                         }
                         mbar_expect_tx(&B->full[slot], KB_BYTES_I);
-                        tma_load_2d(ring + slot * KB_BYTES_I, &tmB, &B->full[slot], kb * 64, (int)(it * BI_TC));
+                        tma_load_2d(ring + slot * KB_BYTES_I, &I.tmB, &B->full[slot], kb * 64, it * BI_TC);
                         ++issued[slot];
                         if (++slot == S) {
                             slot = 0;
@@ -165,10 +181,10 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             }
             // Copies in flight complete on their barriers; wait for them before the CTA exits.
             for (int s = 0; s < S; ++s)
-                if (issued[s] > 0) drain_wait(&B->full[s], (uint32_t)(issued[s] - 1) & 1u, a.st);
+                if (issued[s] > 0) drain_wait(&B->full[s], (uint32_t)(issued[s] - 1) & 1u, st);
             for (int rb = 0; rb < L.nres; ++rb) {
                 const int loads = res_loads / L.nres + (rb < res_loads % L.nres ? 1 : 0);
-                if (loads > 0) drain_wait(&B->res_full[rb], (uint32_t)(loads - 1) & 1u, a.st);
+                if (loads > 0) drain_wait(&B->res_full[rb], (uint32_t)(loads - 1) & 1u, st);
             }
         }
     } else if (warp == 1) {
@@ -178,21 +194,26 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             uint32_t ph = 0, tile_j = 0;
             int iter = 0;
             bool ok = true;
-            for (int64_t ut = blockIdx.x; ut < user_tiles && ok; ut += gridDim.x, ++iter) {
+            DevStatus* st = inst[0].a.st;
+            for (long long w = blockIdx.x; w < total_units && ok; w += gridDim.x, ++iter) {
+                const TcInstance& I = inst[unit_instance(inst, count, w)];
+                st = I.a.st;
+                const int KB = I.a.dp >> 6;
+                const int item_tiles = (int)((I.a.m + BI_TC - 1) / BI_TC);
                 const int rb = iter % L.nres;
-                if (!mbar_wait(&B->res_full[rb], (iter / L.nres) & 1, abort, a.st)) break;
+                if (!mbar_wait(&B->res_full[rb], (iter / L.nres) & 1, abort, st)) break;
                 tc_fence_after();
                 const uint8_t* sAr = sA + rb * L.res_bytes;
-                for (int64_t it = 0; it < item_tiles && ok; ++it) {
+                for (int it = 0; it < item_tiles && ok; ++it) {
                     const uint32_t b = tile_j & 1u, use = tile_j >> 1;
-                    if (!mbar_wait(&B->tempty[b], (use & 1u) ^ 1u, abort, a.st)) {
+                    if (!mbar_wait(&B->tempty[b], (use & 1u) ^ 1u, abort, st)) {
                         ok = false;
                         break;
                     }
                     tc_fence_after();
                     const uint32_t d = tmem + b * BI_TC;
                     for (int kb = 0; kb < KB; ++kb) {
-                        if (!mbar_wait(&B->full[slot], ph, abort, a.st)) {
+                        if (!mbar_wait(&B->full[slot], ph, abort, st)) {
                             ok = false;
                             break;
                         }
@@ -216,20 +237,21 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                 tc_commit(&B->res_empty[rb]);
             }
             tc_commit(&B->drain);
-            drain_wait(&B->drain, 0u, a.st);
+            drain_wait(&B->drain, 0u, st);
         }
     } else {
         const int ew = warp - 2;          // 0..7
         const int h = ew >> 2;            // warpgroup = accumulator buffer it consumes
         const int q = warp & 3;           // TMEM lane quarter this warp may access
         const int r = q * 32 + lane;      // user row of the tile
-        float* heap = heaps + h * (a.k * BU);
+        float* heap = heaps + h * (kheap * BU);
         uint32_t tile_j = 0;
-        // Bound maxima of this group's first item tile (tile h of the first user tile).
-        const int64_t it0 = (h < item_tiles) ? h : 0;
-        float thm_next = a.thmax[it0], tdl_next = a.tdel[it0];
         bool ok = true;
-        for (int64_t ut = blockIdx.x; ut < user_tiles && ok; ut += gridDim.x) {
+        for (long long w = blockIdx.x; w < total_units && ok; w += gridDim.x) {
+            const TcInstance& I = inst[unit_instance(inst, count, w)];
+            const ThresholdArgs& a = I.a;
+            const long long ut = w - I.unit_begin;
+            const int item_tiles = (int)((a.m + BI_TC - 1) / BI_TC);
             const int64_t u = ut * BU + r;
             const bool active = u < a.n;
             for (int j = 0; j < a.k; ++j) heap[j * BU + r] = -INFINITY;
@@ -241,24 +263,28 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             s.thr = -INFINITY;
             s.cnt = 0;
             s.pub = &Lpub[h * BU + r];
-            s.tag = (unsigned)ut;
-            bool warm = false;  // warm start done for this user tile
+            s.tag = (unsigned)w;
+            bool warm = false;  // warm start done for this unit
             const float un = active ? a.unrm[u] : 0.f;
             const float unh = active ? a.unhat[u] : 0.f;
             const float ud = active ? a.udel[u] : 0.f;
             Cand* mycand = a.cand + ((active ? u : 0) * a.nseg + h) * (int64_t)a.cap;
-            for (int64_t it = 0; it < item_tiles; ++it) {
+            // This group's first tile of the unit, then every other one: the bound maxima of
+            // the next one are loaded while the current one is processed.
+            int itn = (int)((tile_j & 1u) == (uint32_t)h ? 0 : 1);
+            float thm_next = 0.f, tdl_next = 0.f;
+            if (itn < item_tiles) {
+                thm_next = a.thmax[itn];
+                tdl_next = a.tdel[itn];
+            }
+            for (int it = 0; it < item_tiles; ++it) {
                 const uint32_t b = tile_j & 1u, use = tile_j >> 1;
                 ++tile_j;
                 if ((int)b != h) continue;
-                // This group's next tile is two tiles on (wrapping to the next user tile):
-                // start loading its bound maxima now.
                 const float thm = thm_next, tdl = tdl_next;
-                {
-                    int itn = (int)it + 2;
-                    while (itn >= (int)item_tiles) itn -= (int)item_tiles;
-                    thm_next = a.thmax[itn];
-                    tdl_next = a.tdel[itn];
+                if (it + 2 < item_tiles) {
+                    thm_next = a.thmax[it + 2];
+                    tdl_next = a.tdel[it + 2];
                 }
                 if (!mbar_wait(&B->tfull[b], use & 1u, abort, a.st)) {
                     ok = false;
@@ -267,9 +293,9 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                 __syncwarp();
                 tc_fence_after();
                 const float E = err_bound(a.cacc, a.eabs, un, unh, ud, thm, tdl);
-                // The partner's bound may be stale or from this user tile's start (-inf):
+                // The partner's bound may be stale or from this unit's start (-inf):
                 // any value it held is a valid lower bound of tau_u for the current user.
-                s.Lx = read_bound(&Lpub[(1 - h) * BU + r], (unsigned)ut);
+                s.Lx = read_bound(&Lpub[(1 - h) * BU + r], (unsigned)w);
                 const uint32_t tb = tmem + ((uint32_t)(q * 32) << 16) + b * BI_TC;
                 if (!warm) {
                     // First tile of this group for these users: a lockstep first pass over the
@@ -281,7 +307,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                             __syncwarp();
                             tmem_ld32(tb + c0, v);
                         };
-                        const float lw = warm_bound<32, BI_TC>(load, (int)(it * BI_TC), a.m, a.k, E);
+                        const float lw = warm_bound<32, BI_TC>(load, it * BI_TC, a.m, a.k, E);
                         s.Lw = active ? lw : -INFINITY;
                         publish_bound(s.pub, s.tag, s.Lw);
                     }
@@ -299,8 +325,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                     {
                         float v[32];
                         as_floats(ra, v);
-                        sel_chunk(v, active, (int)(it * BI_TC + c0), a.m, E, s, mycand, a.cap, heap, r, a.k,
-                                  a.st);
+                        sel_chunk(v, active, it * BI_TC + c0, a.m, E, s, mycand, a.cap, heap, r, a.k, a.st);
                     }
                     __syncwarp();
                     tmem_wait_bind(rb);
@@ -308,8 +333,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                     {
                         float v[32];
                         as_floats(rb, v);
-                        sel_chunk(v, active, (int)(it * BI_TC + c0 + 32), a.m, E, s, mycand, a.cap, heap, r,
-                                  a.k, a.st);
+                        sel_chunk(v, active, it * BI_TC + c0 + 32, a.m, E, s, mycand, a.cap, heap, r, a.k, a.st);
                     }
                     __syncwarp();
                     if (c0 + 64 < BI_TC) tmem_wait_bind(ra);
@@ -646,16 +670,15 @@ rkm_status make_tmaps(const void* A, int64_t a_rows, const void* B, int64_t b_ro
     return RKM_OK;
 }
 
-void launch_threshold_tc(const ThresholdArgs& a, const void* tmapA, const void* tmapB, cudaStream_t s) {
-    const int KB = a.dp / 64;
-    const TcLayout L = make_layout(KB * KB_BYTES_U, KB_BYTES_I, 2u * BU * a.k * 4u + 2u * BU * 8u, MAX_SLOTS);
+void launch_threshold_tc(const TcInstance* inst, int count, long long total_units, int kheap, int max_dp,
+                         int num_sms, cudaStream_t s) {
+    const int KB = max_dp / 64;
+    const TcLayout L = make_layout(KB * KB_BYTES_U, KB_BYTES_I, 2u * BU * kheap * 4u + 2u * BU * 8u, MAX_SLOTS);
     cudaFuncSetAttribute(k_threshold_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.bytes);
-    const int64_t user_tiles = (a.n + BU - 1) / BU;
-    const int grid = (int)(user_tiles < a.num_sms ? user_tiles : a.num_sms);
+    const int grid = (int)(total_units < num_sms ? total_units : num_sms);
     if (grid < 1) return;
     note_launch();
-    k_threshold_tc<<<grid, TC_THREADS, L.bytes, s>>>(a, *static_cast<const CUtensorMap*>(tmapA),
-                                                      *static_cast<const CUtensorMap*>(tmapB), L);
+    k_threshold_tc<<<grid, TC_THREADS, L.bytes, s>>>(inst, count, total_units, kheap, L);
 }
 
 void launch_count_tc(const CountArgs& a, const void* tmapA, const void* tmapB, cudaStream_t s) {
