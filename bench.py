@@ -44,6 +44,8 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--n", type=int, default=None, help="override the number of users (profiling cases)")
     ap.add_argument("--m", type=int, default=None, help="override the number of items (profiling cases)")
+    ap.add_argument("--requests", type=int, default=2000, help="serve-1m: requests per offered load")
+    ap.add_argument("--slots", type=int, default=2, help="serve-1m: concurrent batches of the serving loop")
     return ap.parse_args()
 
 
@@ -415,6 +417,119 @@ def run_batch(args, rank, local, world):
     print(json.dumps(line), flush=True)
 
 
+def run_serve(args, rank, local, world):
+    """Serving: 1,000,000 resident users (d=100) with thresholds at k=20 against a
+    300,000-item catalogue (computed on the device by rkm_thresholds before timing), then
+    streams of what-if requests (log-uniform sizes in [1, 4096], candidates from the item
+    generator) through the serving loop with host buffers.  First every request is queued at
+    once (saturation: the largest throughput the loop sustains), then Poisson arrivals at 25,
+    50 and 90% of that throughput, each reporting p50/p99 latency (submit -> counts in the
+    caller's buffer).  value = resident users x candidates scored / s at saturation."""
+    import numpy as np
+    import torch
+
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_2504_13445_gb300 as rkm
+    import workloads
+
+    torch.cuda.set_device(local)
+    S = dict(workloads.SERVING)
+    if args.n:
+        S["n"] = args.n
+    if args.m:
+        S["m"] = args.m
+    W = workloads.mf(S["n"], S["m"], S["d"], S["k"], 1, seed=S["catalog_seed"])
+    U = torch.from_numpy(W.U).cuda()
+    P = torch.from_numpy(W.P).cuda()
+    ctx = rkm.Context(args.precision, device=local, profile=True)
+    tau, tid, _ = ctx.thresholds(U, P, W.k)
+    ctx.resident_set(U, tau, tid)
+    del P
+    R = args.requests
+    gaps, sizes, offsets = workloads.serving_stream(R, 1.0, seed=S["query_seed"])
+    Qall = workloads.queries(int(sizes.sum()), W.d, seed=S["query_seed"])
+    reqs = [Qall[o:o + q] for o, q in zip(offsets, sizes)]
+    items_total = int(sizes.sum())
+    mean_q = float(sizes.mean())
+
+    srv = rkm.Server(ctx, slots=args.slots, max_batch_items=8192, memory_bytes=256 << 20)
+
+    def run_stream(arrivals):
+        srv.reset_stats()
+        tickets = [None] * R
+        t0 = time.perf_counter()
+        for j in range(R):
+            if arrivals is not None:
+                delay = arrivals[j] - (time.perf_counter() - t0)
+                if delay > 0:
+                    time.sleep(delay)
+            tickets[j] = srv.submit(reqs[j])
+        for t in tickets:
+            srv.wait(t)
+        return srv.stats()
+
+    for _ in range(max(1, args.warmup)):
+        run_stream(None)
+    clocks = ClockSampler(local)
+    clocks.start()
+    sat = run_stream(None)
+    clk = clocks.stop()
+    loads = []
+    for frac in (0.25, 0.5, 0.9):
+        rate = frac * sat["items_per_s"] / mean_q  # requests per second
+        st = run_stream(gaps / rate)
+        loads.append({"offered_frac_of_saturation": frac, "rate_req_per_s": rate, "p50_ms": st["p50_ms"],
+                      "p99_ms": st["p99_ms"], "mean_ms": st["mean_ms"], "max_ms": st["max_ms"],
+                      "items_per_s": st["items_per_s"], "mean_batch_items": st["mean_batch_items"],
+                      "max_in_flight": st["max_in_flight"]})
+    srv.close()
+
+    # The dominant kernel (the counting product of one full batch of 8192 candidates), timed
+    # alone with CUDA events around each phase.
+    Qb = torch.from_numpy(np.ascontiguousarray(Qall[:8192])).cuda()
+    ctx.query_new_items(Qb)
+    cms = []
+    for _ in range(5):
+        ctx.query_new_items(Qb)
+        cms.append(ctx.stats()["phase_ms"]["count"])
+    qst = ctx.stats()
+    count_ms = statistics.median(cms)
+    flops = 2.0 * qst["pairs_evaluated"] * W.d
+    achieved = flops / (count_ms / 1000) / 1e12
+    peaks = measured_peaks()
+    peak = peaks["bf16_tflops"] if args.precision == "bf16" else fp32_alu_peak_tflops(peaks.get("sm_max_mhz", 2070.0))
+    roof = {"bound": "tensor" if args.precision == "bf16" else "alu",
+            "kernel": "k_count_tc (counting product + classify)" if args.precision == "bf16" else
+                      "k_count_simt (counting product + classify)",
+            "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
+            "peak_source": f"{peaks['source']} bf16_tflops (burst)" if args.precision == "bf16" else "FP32 ALU",
+            "kernel_ms": count_ms, "algorithmic_flops_per_launch": flops,
+            "units": "2 d FLOP per evaluated (user, candidate) pair, 8192 candidates"}
+    if rank != 0:
+        return
+    value = world * sat["pairs_per_s"]
+    req_bytes = mean_q * W.d * 4
+    line = {"metric": "user-item pairs scored/sec (serving what-if queries)", "value": value, "unit": UNIT,
+            "n_gpus": world, "steps": R, "warmup": max(1, args.warmup),
+            "ms_per_step": sat["window_ms"] / R, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "bf16" if args.precision == "bf16" else "f32", "data": "synthetic",
+            "config": {"workload": "serve-1m", "users": W.n, "catalogue": W.m, "d": W.d, "k": W.k,
+                       "requests": R, "candidates": items_total, "sizes": "log-uniform [1, 4096]",
+                       "slots": args.slots, "max_batch_items": 8192, "arena_bytes": 256 << 20,
+                       "step": "one request",
+                       "l2": "not flushed: the resident users (1M x 128 BF16 = 256 MB) exceed L2, so every"
+                             " batch streams them from HBM"},
+            "serving": {"saturation": {k: sat[k] for k in ("items_per_s", "p50_ms", "p99_ms", "mean_batch_items",
+                                                            "batches", "max_in_flight", "window_ms")},
+                        "loads": loads},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": int(req_bytes),
+                    "d2h_bytes_per_step": int(mean_q * 4),
+                    "api": "rkm_serve_submit/rkm_serve_wait with host buffers (value is end to end)"},
+            "roofline": roof, "gpu_launches": int(sat["kernel_launches"]), "clocks": clk}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     rank, local, world = dist_init()
@@ -422,6 +537,8 @@ def main():
         run_reference(args, rank, world)
     elif args.workload == "batch-64":
         run_batch(args, rank, local, world)
+    elif args.workload == "serve-1m":
+        run_serve(args, rank, local, world)
     else:
         run_ours(args, rank, local, world)
     if world > 1:

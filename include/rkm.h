@@ -61,7 +61,8 @@ typedef enum {
     RKM_EOVERFLOW = 4,  /* a candidate or band buffer overflowed after retries  */
     RKM_ETIMEOUT = 5,   /* a bounded device wait gave up                        */
     RKM_ESTATE = 6,     /* call out of order (e.g. query before resident set)   */
-    RKM_EINTERNAL = 7   /* a device-side consistency check failed               */
+    RKM_EINTERNAL = 7,  /* a device-side consistency check failed               */
+    RKM_EBUSY = 8       /* serving: the request queue is full; submit again later */
 } rkm_status;
 
 typedef enum {
@@ -240,6 +241,84 @@ RKM_API rkm_status rkm_topn_batch(rkm_ctx* ctx, const rkm_instance* inst, int co
  */
 RKM_API rkm_status rkm_topn_scores_noalloc(const int32_t* scores, int64_t m, int N, int32_t* ids,
                                            int32_t* top_scores, void* stream);
+
+/*
+ * Serving loop -- a request loop over the resident users and thresholds of a context (set by
+ * rkm_resident_set), scoring new candidate items as rkm_query_new_items does.  Requests are
+ * queued by rkm_serve_submit and served by `slots` worker threads, each with its own CUDA
+ * stream and workspace.  A worker that becomes free takes the oldest waiting requests, as
+ * many as fit both `max_batch_items` candidates and the free part of a device arena of
+ * `memory_bytes` that holds the admitted requests' candidate rows and counts (continuous
+ * batching: requests that arrive while other batches are on the GPU join the next batch
+ * that a slot and memory allow), copies them to the device, runs one counting pass over the
+ * users for the whole batch, and hands each request its counts.  Batches of different slots
+ * overlap on the device.  A request's counts do not depend on which batch it joins.
+ *
+ * The server borrows the context: while it exists, the context's resident users must not be
+ * replaced (rkm_resident_set returns RKM_ESTATE) and the context must not be destroyed.
+ * Server calls are thread-safe; any host thread may submit and wait.
+ */
+typedef struct rkm_server rkm_server;
+
+typedef struct {
+    int slots;               /* concurrent batches (worker threads + streams); default 2, 1..16   */
+    int64_t max_batch_items; /* candidates per batch, and the largest request; default 8192      */
+    int64_t memory_bytes;    /* device arena for admitted requests' rows and counts; default
+                                64 MiB.  A request needing more is rejected (RKM_EINVAL).         */
+    int64_t max_pending;     /* requests queued (not yet admitted) before submit returns
+                                RKM_EBUSY; default 1048576                                      */
+} rkm_serve_opts;
+
+typedef struct {
+    uint64_t submitted;        /* requests accepted since the last reset                         */
+    uint64_t completed;        /* requests finished, including failed ones                      */
+    uint64_t failed;           /* requests finished with an error status                        */
+    uint64_t items;            /* candidates scored by completed requests                       */
+    uint64_t batches;          /* counting passes over the resident users                       */
+    double mean_batch_items;   /* items / batches                                                */
+    double p50_ms, p99_ms;     /* latency percentiles (nearest rank): submit -> counts written  */
+    double mean_ms, max_ms;    /* mean and largest latency                                       */
+    double mean_queue_ms;      /* submit -> admission into a batch, averaged                     */
+    double window_ms;          /* first submission -> last completion                            */
+    double items_per_s;        /* items / window                                                 */
+    double pairs_per_s;        /* resident users * items / window                                */
+    int64_t arena_peak_bytes;  /* most arena bytes held by admitted requests at once              */
+    int32_t max_in_flight;     /* most batches admitted and not yet finished at once             */
+    int32_t slots;             /* worker slots of the server                                      */
+    uint64_t kernel_launches;  /* kernels launched by all slots since the last reset             */
+} rkm_serve_stats;
+
+/* Fill `opts` with the defaults listed above. */
+RKM_API void rkm_serve_default_opts(rkm_serve_opts* opts);
+
+/* Start a server on `ctx`, whose resident set must exist (else RKM_ESTATE).  `opts` may be
+ * NULL.  Allocates the arena, each slot's workspace (sized by one warm-up pass of
+ * max_batch_items zero candidates) and pinned staging, then starts the worker threads. */
+RKM_API rkm_status rkm_serve_create(rkm_server** out, rkm_ctx* ctx, const rkm_serve_opts* opts);
+
+/* Queue one request: Q host [q x d] FP32 (stride ldq >= d, d = the resident users' d),
+ * 1 <= q <= max_batch_items; counts host [q] int32 receives #{u : u.Q_j > tau_u}.  Both
+ * buffers are borrowed until rkm_serve_wait reports the ticket finished.  Returns RKM_EBUSY
+ * when max_pending requests are waiting, RKM_ESTATE after the server started stopping. */
+RKM_API rkm_status rkm_serve_submit(rkm_server* srv, const float* Q, int64_t q, int64_t ldq, int32_t* counts,
+                                    uint64_t* ticket);
+
+/* Wait for a request.  timeout_ms < 0 waits without limit.  Returns the request's own status
+ * (its error message becomes this thread's rkm_last_error) and releases the ticket; returns
+ * RKM_ETIMEOUT, keeping the ticket, if it has not finished in time; RKM_EINVAL for an unknown
+ * ticket.  latency_ms (may be NULL) receives submit -> finish. */
+RKM_API rkm_status rkm_serve_wait(rkm_server* srv, uint64_t ticket, double timeout_ms, double* latency_ms);
+
+/* Block until no request is queued or running. */
+RKM_API rkm_status rkm_serve_drain(rkm_server* srv);
+
+/* Counters since creation or the last rkm_serve_reset_stats. */
+RKM_API rkm_status rkm_serve_get_stats(rkm_server* srv, rkm_serve_stats* out);
+RKM_API rkm_status rkm_serve_reset_stats(rkm_server* srv);
+
+/* Finish every queued request, stop the workers and free the server (tickets not yet waited
+ * for are released).  NULL is accepted. */
+RKM_API void rkm_serve_destroy(rkm_server* srv);
 
 #ifdef __cplusplus
 }

@@ -18,12 +18,14 @@ LIB_PATH = os.path.join(HERE, "lib", "librkm.so")
 RKM_FP32, RKM_BF16, RKM_FP8 = 0, 1, 2
 PRECISIONS = {"fp32": RKM_FP32, "bf16": RKM_BF16, "fp8": RKM_FP8}
 STATUS = {0: "RKM_OK", 1: "RKM_EINVAL", 2: "RKM_ENOMEM", 3: "RKM_ECUDA", 4: "RKM_EOVERFLOW",
-          5: "RKM_ETIMEOUT", 6: "RKM_ESTATE", 7: "RKM_EINTERNAL"}
+          5: "RKM_ETIMEOUT", 6: "RKM_ESTATE", 7: "RKM_EINTERNAL", 8: "RKM_EBUSY"}
 
 EXPORTED = ["rkm_default_opts", "rkm_create", "rkm_destroy", "rkm_last_error", "rkm_version",
             "rkm_thresholds", "rkm_scores", "rkm_topn", "rkm_topn_host", "rkm_item_bounds",
             "rkm_resident_set", "rkm_query_new_items", "rkm_get_stats", "rkm_topn_scores_noalloc",
-            "rkm_topn_batch"]
+            "rkm_topn_batch", "rkm_serve_default_opts", "rkm_serve_create", "rkm_serve_submit",
+            "rkm_serve_wait", "rkm_serve_drain", "rkm_serve_get_stats", "rkm_serve_reset_stats",
+            "rkm_serve_destroy"]
 
 
 class RkmError(RuntimeError):
@@ -61,6 +63,24 @@ class Stats(ctypes.Structure):
         return out
 
 
+class ServeOpts(ctypes.Structure):
+    _fields_ = [("slots", ctypes.c_int), ("max_batch_items", ctypes.c_int64), ("memory_bytes", ctypes.c_int64),
+                ("max_pending", ctypes.c_int64)]
+
+
+class ServeStats(ctypes.Structure):
+    _fields_ = [("submitted", ctypes.c_uint64), ("completed", ctypes.c_uint64), ("failed", ctypes.c_uint64),
+                ("items", ctypes.c_uint64), ("batches", ctypes.c_uint64), ("mean_batch_items", ctypes.c_double),
+                ("p50_ms", ctypes.c_double), ("p99_ms", ctypes.c_double), ("mean_ms", ctypes.c_double),
+                ("max_ms", ctypes.c_double), ("mean_queue_ms", ctypes.c_double), ("window_ms", ctypes.c_double),
+                ("items_per_s", ctypes.c_double), ("pairs_per_s", ctypes.c_double),
+                ("arena_peak_bytes", ctypes.c_int64), ("max_in_flight", ctypes.c_int32),
+                ("slots", ctypes.c_int32), ("kernel_launches", ctypes.c_uint64)]
+
+    def as_dict(self) -> dict:
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
 _lib = None
 
 
@@ -89,6 +109,14 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         "rkm_get_stats": (I, [P, ctypes.POINTER(Stats)]),
         "rkm_topn_scores_noalloc": (I, [P, I64, I, P, P, P]),
         "rkm_topn_batch": (I, [P, ctypes.POINTER(Instance), I, P]),
+        "rkm_serve_default_opts": (V, [ctypes.POINTER(ServeOpts)]),
+        "rkm_serve_create": (I, [ctypes.POINTER(P), P, ctypes.POINTER(ServeOpts)]),
+        "rkm_serve_submit": (I, [P, P, I64, I64, P, ctypes.POINTER(ctypes.c_uint64)]),
+        "rkm_serve_wait": (I, [P, ctypes.c_uint64, ctypes.c_double, ctypes.POINTER(ctypes.c_double)]),
+        "rkm_serve_drain": (I, [P]),
+        "rkm_serve_get_stats": (I, [P, ctypes.POINTER(ServeStats)]),
+        "rkm_serve_reset_stats": (I, [P]),
+        "rkm_serve_destroy": (V, [P]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -263,6 +291,64 @@ def rkm_topn_scores_noalloc(scores, N: int):
     return ids, top
 
 
+def rkm_serve_default_opts() -> ServeOpts:
+    o = ServeOpts()
+    load_library().rkm_serve_default_opts(ctypes.byref(o))
+    return o
+
+
+def rkm_serve_create(ctx, slots: int | None = None, max_batch_items: int | None = None,
+                     memory_bytes: int | None = None, max_pending: int | None = None) -> ctypes.c_void_p:
+    o = rkm_serve_default_opts()
+    for name, v in (("slots", slots), ("max_batch_items", max_batch_items), ("memory_bytes", memory_bytes),
+                    ("max_pending", max_pending)):
+        if v is not None:
+            setattr(o, name, v)
+    h = ctypes.c_void_p()
+    _check(load_library().rkm_serve_create(ctypes.byref(h), ctx, ctypes.byref(o)))
+    return h
+
+
+def rkm_serve_submit(srv, Q, counts) -> int:
+    """Q: host float32 [q, d] (numpy, unit column stride); counts: host int32 [q].  Both must
+    stay alive until rkm_serve_wait returns for the ticket."""
+    import numpy as np
+    if not (isinstance(Q, np.ndarray) and Q.dtype == np.float32 and Q.ndim == 2 and Q.strides[1] == 4):
+        raise TypeError("Q must be a 2-D float32 numpy array with unit column stride")
+    if not (isinstance(counts, np.ndarray) and counts.dtype == np.int32 and counts.flags.c_contiguous
+            and counts.size >= Q.shape[0]):
+        raise TypeError("counts must be a contiguous int32 numpy array of q entries")
+    t = ctypes.c_uint64()
+    _check(load_library().rkm_serve_submit(srv, Q.ctypes.data, Q.shape[0], Q.strides[0] // 4,
+                                           counts.ctypes.data, ctypes.byref(t)))
+    return t.value
+
+
+def rkm_serve_wait(srv, ticket: int, timeout_ms: float = -1.0) -> float:
+    """Returns the request's latency in ms; raises RkmError with the request's status."""
+    lat = ctypes.c_double()
+    _check(load_library().rkm_serve_wait(srv, ticket, timeout_ms, ctypes.byref(lat)))
+    return lat.value
+
+
+def rkm_serve_drain(srv) -> None:
+    _check(load_library().rkm_serve_drain(srv))
+
+
+def rkm_serve_get_stats(srv) -> dict:
+    s = ServeStats()
+    _check(load_library().rkm_serve_get_stats(srv, ctypes.byref(s)))
+    return s.as_dict()
+
+
+def rkm_serve_reset_stats(srv) -> None:
+    _check(load_library().rkm_serve_reset_stats(srv))
+
+
+def rkm_serve_destroy(srv) -> None:
+    load_library().rkm_serve_destroy(srv)
+
+
 def rkm_version() -> str:
     return load_library().rkm_version().decode()
 
@@ -317,3 +403,56 @@ class Context:
 
     def stats(self) -> dict:
         return rkm_get_stats(self.handle)
+
+
+class Server:
+    """Serving loop over a Context's resident set (rkm_serve_*).  Requests are host numpy
+    arrays; submit returns a ticket, wait returns (counts, latency_ms)."""
+
+    def __init__(self, ctx: Context, **opts):
+        self.ctx = ctx
+        self.handle = rkm_serve_create(ctx.handle, **opts)
+        self._held = {}
+
+    def submit(self, Q) -> int:
+        import numpy as np
+        counts = np.empty(Q.shape[0], dtype=np.int32)
+        t = rkm_serve_submit(self.handle, Q, counts)
+        self._held[t] = (Q, counts)
+        return t
+
+    def wait(self, ticket: int, timeout_ms: float = -1.0):
+        try:
+            lat = rkm_serve_wait(self.handle, ticket, timeout_ms)
+        except RkmError as e:
+            if e.status != 5:  # the library released the ticket unless the wait timed out
+                self._held.pop(ticket, None)
+            raise
+        return self._held.pop(ticket)[1], lat
+
+    def drain(self) -> None:
+        rkm_serve_drain(self.handle)
+
+    def stats(self) -> dict:
+        return rkm_serve_get_stats(self.handle)
+
+    def reset_stats(self) -> None:
+        rkm_serve_reset_stats(self.handle)
+
+    def close(self) -> None:
+        if self.handle:
+            rkm_serve_destroy(self.handle)
+            self.handle = None
+            self._held.clear()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()

@@ -12,7 +12,7 @@ CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "lib")
 BUILD_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "librkm.so")
-SOURCES = ["api.cu", "prep.cu", "simt.cu", "exact.cu", "topn.cu", "tc.cu", "noalloc.cu"]
+SOURCES = ["api.cu", "prep.cu", "simt.cu", "exact.cu", "topn.cu", "tc.cu", "noalloc.cu", "serve.cpp"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-fvisibility=hidden",
               "--expt-relaxed-constexpr"]
@@ -42,7 +42,7 @@ def build(verbose: bool = False, extra_flags: list[str] | None = None) -> str:
 
     def compile_one(src: str) -> str:
         path = os.path.join(CSRC, src)
-        obj = os.path.join(BUILD_DIR, src.replace(".cu", ".o"))
+        obj = os.path.join(BUILD_DIR, os.path.splitext(src)[0] + ".o")
         if _stale(obj, [path] + headers):
             cmd = [cc, *ARCH, *flags, "-c", path, "-o", obj]
             if verbose:

@@ -25,6 +25,7 @@
 
 #include "../../include/rkm.h"
 #include "common.cuh"
+#include "internal.h"
 #include "kernels.h"
 #include "tmap.h"
 
@@ -97,6 +98,7 @@ struct rkm_ctx {
         tid_tmp;
     // serving (resident users)
     bool resident = false;
+    std::atomic<int> servers{0};  // serving loops borrowing the resident set
     int64_t res_n = 0;
     int res_d = 0;
     unsigned res_off_grid = 0;
@@ -687,6 +689,67 @@ double now_ms() {
 
 }  // namespace
 
+rkm_status rkm::query_resident(rkm_ctx* c, const rkm_ctx* r, const float* Q, int64_t q, int64_t ldq, int32_t* counts,
+                               cudaStream_t s) {
+    if (!c || !r) return fail(RKM_EINVAL, "null context");
+    if (!r->resident) return fail(RKM_ESTATE, "rkm_query_new_items before rkm_resident_set");
+    const int d = r->res_d;
+    TRY(check_common(c, d));
+    TRY(check_matrix(Q, q, ldq, d, "Q"));
+    if (q > 0 && !counts) return fail(RKM_EINVAL, "null counts");
+    const double t0 = now_ms();
+    reset_stats(c);
+    if (q == 0) return RKM_OK;
+    const int64_t n = r->res_n;
+    if (n == 0) {
+        CUDA_TRY(cudaMemsetAsync(counts, 0, q * sizeof(int32_t), s));
+        CUDA_TRY(cudaStreamSynchronize(s));
+        return RKM_OK;
+    }
+    const PathShape ps = path_shape(c->opts.precision, d);
+    init_caps(c, std::max<int64_t>(n / 64, q * 64), 1);
+    TRY(begin_call(c, s));
+    if (r->res_off_grid) CUDA_TRY(cudaMemsetAsync(&c->st->off_grid, 1, 1, s));
+    ItemSide it;
+    {
+        Phase ph(c, s, RKM_PHASE_PREP);
+        TRY(prep_items(c, ps, Q, q, ldq, d, query_bufs(c), &it, s));
+    }
+    UserOrder uo{static_cast<int*>(r->res_uperm.p), static_cast<unsigned*>(r->res_ucum.p), r->res_pack.p,
+                 static_cast<UserMeta*>(r->res_meta.p)};
+    ExactData x{static_cast<const float*>(r->res_U.p), d, static_cast<const int*>(r->res_e.p),
+                static_cast<const int16_t*>(r->res_q.p), Q, ldq, it.rp.e, it.rp.q, d, (int)round_up(d, 8),
+                &c->st->off_grid};
+    int* cnt;
+    TRY(c->ensure(c->q_cnt, q, &cnt));
+    for (int attempt = 0;; ++attempt) {
+        int2* band;
+        TRY(ensure_band(c, &band));
+        CUDA_TRY(cudaMemsetAsync(cnt, 0, q * sizeof(int), s));
+        CUDA_TRY(cudaMemsetAsync(&c->st->band_count, 0, 2 * sizeof(unsigned), s));
+        const double* rtau = static_cast<const double*>(r->res_tau.p);
+        const int* rtid = static_cast<const int*>(r->res_tid.p);
+        TRY(count_stage(c, ps, n, uo, it, true, 0, (int)it.tiles, false, x, rtau, rtid, cnt, band, s));
+        TRY(band_stage(c, it, true, x, rtau, rtid, cnt, band, s));
+        scatter_i32(cnt, it.perm, q, counts, s);
+        TRY(read_status(c, s));
+        if (!c->st_host->band_overflow) break;
+        if (attempt >= 3) return fail(RKM_EOVERFLOW, "band queue overflowed");
+        c->band_cap = std::min<int64_t>((int64_t)UINT32_MAX - 1,
+                                        std::max<int64_t>(c->band_cap * 2, (int64_t)c->st_host->band_count + 1024));
+        c->stats.retries++;
+        CUDA_TRY(cudaMemsetAsync(&c->st->band_overflow, 0, sizeof(unsigned), s));
+    }
+    if (c->st_host->internal_error) return fail(RKM_EINTERNAL, "query: device consistency check failed");
+    c->stats.pairs_total = (uint64_t)n * (uint64_t)q;
+    c->stats.pairs_evaluated = c->st_host->pairs_evaluated;
+    c->stats.band_pairs = c->st_host->band_count;
+    c->stats.exact_integer_path = c->st_host->off_grid ? 0 : 1;
+    c->stats.last_ms = now_ms() - t0;
+    return RKM_OK;
+}
+
+
 extern "C" {
 
 void rkm_default_opts(rkm_opts* o) {
@@ -1023,6 +1086,7 @@ rkm_status rkm_resident_set(rkm_ctx* c, const float* U, int64_t n, int64_t ldu, 
     TRY(check_common(c, d));
     TRY(check_matrix(U, n, ldu, d, "U"));
     if (n > 0 && (!tau || !tid)) return fail(RKM_EINVAL, "null tau/tid");
+    if (c->servers.load() != 0) return fail(RKM_ESTATE, "the resident set is in use by a serving loop");
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     c->resident = false;
     const PathShape ps = path_shape(c->opts.precision, d);
@@ -1055,62 +1119,7 @@ rkm_status rkm_resident_set(rkm_ctx* c, const float* U, int64_t n, int64_t ldu, 
 
 rkm_status rkm_query_new_items(rkm_ctx* c, const float* Q, int64_t q, int64_t ldq, int32_t* counts, void* stream) {
     if (!c) return fail(RKM_EINVAL, "null context");
-    if (!c->resident) return fail(RKM_ESTATE, "rkm_query_new_items before rkm_resident_set");
-    const int d = c->res_d;
-    TRY(check_common(c, d));
-    TRY(check_matrix(Q, q, ldq, d, "Q"));
-    if (q > 0 && !counts) return fail(RKM_EINVAL, "null counts");
-    const double t0 = now_ms();
-    reset_stats(c);
-    if (q == 0) return RKM_OK;
-    cudaStream_t s = static_cast<cudaStream_t>(stream);
-    const int64_t n = c->res_n;
-    if (n == 0) {
-        CUDA_TRY(cudaMemsetAsync(counts, 0, q * sizeof(int32_t), s));
-        CUDA_TRY(cudaStreamSynchronize(s));
-        return RKM_OK;
-    }
-    const PathShape ps = path_shape(c->opts.precision, d);
-    init_caps(c, std::max<int64_t>(n / 64, q * 64), 1);
-    TRY(begin_call(c, s));
-    if (c->res_off_grid) CUDA_TRY(cudaMemsetAsync(&c->st->off_grid, 1, 1, s));
-    ItemSide it;
-    {
-        Phase ph(c, s, RKM_PHASE_PREP);
-        TRY(prep_items(c, ps, Q, q, ldq, d, query_bufs(c), &it, s));
-    }
-    UserOrder uo{static_cast<int*>(c->res_uperm.p), static_cast<unsigned*>(c->res_ucum.p), c->res_pack.p,
-                 static_cast<UserMeta*>(c->res_meta.p)};
-    ExactData x{static_cast<const float*>(c->res_U.p), d, static_cast<const int*>(c->res_e.p),
-                static_cast<const int16_t*>(c->res_q.p), Q, ldq, it.rp.e, it.rp.q, d, (int)round_up(d, 8),
-                &c->st->off_grid};
-    int* cnt;
-    TRY(c->ensure(c->q_cnt, q, &cnt));
-    for (int attempt = 0;; ++attempt) {
-        int2* band;
-        TRY(ensure_band(c, &band));
-        CUDA_TRY(cudaMemsetAsync(cnt, 0, q * sizeof(int), s));
-        CUDA_TRY(cudaMemsetAsync(&c->st->band_count, 0, 2 * sizeof(unsigned), s));
-        const double* rtau = static_cast<const double*>(c->res_tau.p);
-        const int* rtid = static_cast<const int*>(c->res_tid.p);
-        TRY(count_stage(c, ps, n, uo, it, true, 0, (int)it.tiles, false, x, rtau, rtid, cnt, band, s));
-        TRY(band_stage(c, it, true, x, rtau, rtid, cnt, band, s));
-        scatter_i32(cnt, it.perm, q, counts, s);
-        TRY(read_status(c, s));
-        if (!c->st_host->band_overflow) break;
-        if (attempt >= 3) return fail(RKM_EOVERFLOW, "band queue overflowed");
-        c->band_cap = std::min<int64_t>((int64_t)UINT32_MAX - 1,
-                                        std::max<int64_t>(c->band_cap * 2, (int64_t)c->st_host->band_count + 1024));
-        c->stats.retries++;
-        CUDA_TRY(cudaMemsetAsync(&c->st->band_overflow, 0, sizeof(unsigned), s));
-    }
-    if (c->st_host->internal_error) return fail(RKM_EINTERNAL, "query: device consistency check failed");
-    c->stats.pairs_total = (uint64_t)n * (uint64_t)q;
-    c->stats.pairs_evaluated = c->st_host->pairs_evaluated;
-    c->stats.band_pairs = c->st_host->band_count;
-    c->stats.exact_integer_path = c->st_host->off_grid ? 0 : 1;
-    c->stats.last_ms = now_ms() - t0;
-    return RKM_OK;
+    return rkm::query_resident(c, c, Q, q, ldq, counts, static_cast<cudaStream_t>(stream));
 }
 
 }  // extern "C"
@@ -1134,6 +1143,26 @@ rkm_ctx* make_sub(const rkm_ctx* parent) {
     }
     return c;
 }
+
+}  // namespace
+
+rkm_ctx* rkm::worker_context(const rkm_ctx* parent) { return make_sub(parent); }
+
+bool rkm::resident_shape(const rkm_ctx* c, int64_t* n, int* d, int* device) {
+    if (!c || !c->resident) return false;
+    *n = c->res_n;
+    *d = c->res_d;
+    *device = c->device;
+    return true;
+}
+
+void rkm::attach_server(rkm_ctx* c, int delta) { c->servers.fetch_add(delta); }
+
+rkm_status rkm::fail_with(rkm_status s, const char* msg) { return fail(s, "%s", msg); }
+
+unsigned long long rkm::launch_count() { return g_launches.load(); }
+
+namespace {
 
 struct InstWork {
     PathShape ps;

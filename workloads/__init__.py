@@ -119,7 +119,7 @@ def mf_like(n: int, d: int, seed: int, tag: int, norm_sigma: float,
     return out
 
 
-TAG_USERS, TAG_ITEMS, TAG_QUERIES = 1, 2, 3
+TAG_USERS, TAG_ITEMS, TAG_QUERIES, TAG_SERVING = 1, 2, 3, 4
 
 
 @dataclass
@@ -200,3 +200,26 @@ def batching_instances(count: int = 64, base_seed: int = 1000) -> list[dict]:
         k = (5, 10, 25)[min(2, int(u[3] * 3))]
         out.append(dict(n=n, m=m, d=d, k=k, N=20, seed=base_seed + j))
     return out
+
+
+# The serving workload: resident users and the catalogue their thresholds come from, then a
+# stream of what-if requests whose candidate rows come from the query stream of query_seed.
+SERVING = dict(n=1_000_000, m=300_000, d=100, k=20, catalog_seed=3, query_seed=4)
+
+
+def serving_stream(count: int, rate_per_s: float, seed: int = 4, max_q: int = 4096):
+    """Poisson arrivals of `count` requests at `rate_per_s` (exponential gaps; rate <= 0 puts
+    every arrival at time 0) with sizes log-uniform over [1, max_q]:
+    q = min(max_q, floor(exp(U * ln(max_q + 1)))) for U uniform in (0, 1).  Request j's
+    candidates are rows offsets[j] .. offsets[j] + sizes[j] - 1 of queries(.., seed).
+    Returns (arrival times in seconds, sizes, offsets) as numpy arrays."""
+    key = stream_key(seed, TAG_SERVING)
+    u = uniform53(key, 0, 2 * count).reshape(count, 2)
+    sizes = np.minimum(max_q, np.floor(np.exp(u[:, 0] * math.log(max_q + 1.0)))).astype(np.int64)
+    sizes = np.maximum(sizes, 1)
+    if rate_per_s > 0:
+        arrivals = np.cumsum(-np.log(u[:, 1]) / rate_per_s)
+    else:
+        arrivals = np.zeros(count)
+    offsets = np.concatenate([[0], np.cumsum(sizes)[:-1]]).astype(np.int64)
+    return arrivals, sizes, offsets
