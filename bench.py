@@ -37,7 +37,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--precision", default="bf16", choices=["bf16", "fp32"])
+    ap.add_argument("--precision", default="bf16", choices=["bf16", "fp8", "fp32"])
     ap.add_argument("--workload", default="mf-500k")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
@@ -157,6 +157,18 @@ def threshold_traffic(workload: str):
         with open(os.path.join(ROOT, "paper_2504_13445_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return THRESHOLD_TRAFFIC.get(h.hexdigest(), {}).get(workload)
+
+
+def tensor_peak(peaks: dict, precision: str):
+    """Dense tensor peak of the product's dtype: the measured BF16 burst figure, times the
+    nominal FP8/BF16 ratio (4.5 / 2.25 PFLOP/s) for FP8."""
+    bf16 = peaks["bf16_tflops"]
+    if precision == "fp8":
+        return 2.0 * bf16, f"{peaks['source']} bf16_tflops (burst) x 2 (nominal FP8/BF16 dense ratio)"
+    return bf16, f"{peaks['source']} bf16_tflops (burst)"
+
+
+DTYPE = {"bf16": "bf16", "fp8": "e4m3", "fp32": "f32"}
 
 
 def fp32_alu_peak_tflops(sm_mhz: float, sms: int = 152) -> float:
@@ -318,12 +330,13 @@ def run_ours(args, rank, local, world):
     thr_avg = statistics.mean(t / max(1, l) for t, l in zip(thr_ms, thr_launch))
     flops = 2.0 * W.n * W.m * W.d
     achieved = flops / (thr_avg / 1000) / 1e12
-    if args.precision == "bf16":
-        peak = peaks["bf16_tflops"]
+    if args.precision in ("bf16", "fp8"):
+        peak, src = tensor_peak(peaks, args.precision)
         roof = {"bound": "tensor", "kernel": "k_threshold_tc (threshold product + selector)",
                 "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-                "traffic": threshold_traffic(args.workload) if not (args.n or args.m) else None,
-                "peak_source": f"{peaks['source']} bf16_tflops (burst)"}
+                "traffic": threshold_traffic(args.workload) if not (args.n or args.m) and args.precision == "bf16"
+                else None,
+                "peak_source": src}
     else:
         sm_mhz = peaks.get("sm_max_mhz", 2070.0)
         peak = fp32_alu_peak_tflops(sm_mhz)
@@ -334,7 +347,7 @@ def run_ours(args, rank, local, world):
     roof["algorithmic_flops_per_launch"] = flops
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "bf16" if args.precision == "bf16" else "f32",
+            "vs_baseline": None, "dtype": DTYPE[args.precision],
             "data": "synthetic",
             "config": {"workload": args.workload if not (args.n or args.m) else f"{args.workload} resized",
                        "n": W.n, "m": W.m, "d": W.d, "k": W.k, "N": W.N,
@@ -344,7 +357,9 @@ def run_ours(args, rank, local, world):
             "roofline": roof,
             "gpu_launches": int(launches),
             "clocks": clk,
-            "detail": {"items_counted_mean": statistics.mean(counted), "candidates_mean": statistics.mean(cand),
+            "detail": {"band_hit_fraction": statistics.mean(band) / max(1.0, statistics.mean(evald)),
+                       "candidates_per_user": statistics.mean(cand) / W.n,
+                       "items_counted_mean": statistics.mean(counted), "candidates_mean": statistics.mean(cand),
                        "band_pairs_mean": statistics.mean(band), "pairs_evaluated_mean": statistics.mean(evald),
                        "retries_last_step": st["retries"], "phase_ms_last_step": st["phase_ms"]}}
     if e2e:
@@ -406,7 +421,7 @@ def run_batch(args, rank, local, world):
         return
     line = {"metric": METRIC, "value": world * pairs / (ms / 1000), "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "bf16" if args.precision == "bf16" else "f32",
+            "scaling": "weak", "vs_baseline": None, "dtype": DTYPE[args.precision],
             "data": "synthetic",
             "config": {"workload": "batch-64", "instances": len(sizes), "pairs": pairs,
                        "users": sum(sz["n"] for sz in sizes), "items": sum(sz["m"] for sz in sizes),
@@ -498,12 +513,15 @@ def run_serve(args, rank, local, world):
     flops = 2.0 * qst["pairs_evaluated"] * W.d
     achieved = flops / (count_ms / 1000) / 1e12
     peaks = measured_peaks()
-    peak = peaks["bf16_tflops"] if args.precision == "bf16" else fp32_alu_peak_tflops(peaks.get("sm_max_mhz", 2070.0))
-    roof = {"bound": "tensor" if args.precision == "bf16" else "alu",
-            "kernel": "k_count_tc (counting product + classify)" if args.precision == "bf16" else
-                      "k_count_simt (counting product + classify)",
+    tc = args.precision in ("bf16", "fp8")
+    if tc:
+        peak, src = tensor_peak(peaks, args.precision)
+    else:
+        peak, src = fp32_alu_peak_tflops(peaks.get("sm_max_mhz", 2070.0)), "FP32 ALU"
+    roof = {"bound": "tensor" if tc else "alu",
+            "kernel": "k_count_tc (counting product + classify)" if tc else "k_count_simt (counting product + classify)",
             "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
-            "peak_source": f"{peaks['source']} bf16_tflops (burst)" if args.precision == "bf16" else "FP32 ALU",
+            "peak_source": src,
             "kernel_ms": count_ms, "algorithmic_flops_per_launch": flops,
             "units": "2 d FLOP per evaluated (user, candidate) pair, 8192 candidates"}
     if rank != 0:
@@ -513,7 +531,7 @@ def run_serve(args, rank, local, world):
     line = {"metric": "user-item pairs scored/sec (serving what-if queries)", "value": value, "unit": UNIT,
             "n_gpus": world, "steps": R, "warmup": max(1, args.warmup),
             "ms_per_step": sat["window_ms"] / R, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "bf16" if args.precision == "bf16" else "f32", "data": "synthetic",
+            "vs_baseline": None, "dtype": DTYPE[args.precision], "data": "synthetic",
             "config": {"workload": "serve-1m", "users": W.n, "catalogue": W.m, "d": W.d, "k": W.k,
                        "requests": R, "candidates": items_total, "sizes": "log-uniform [1, 4096]",
                        "slots": args.slots, "max_batch_items": 8192, "arena_bytes": 256 << 20,

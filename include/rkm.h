@@ -69,7 +69,9 @@ typedef enum {
     RKM_FP32 = 0,  /* FP32 CUDA-core products, FP64/integer exact rescoring       */
     RKM_BF16 = 1,  /* BF16 tensor-core (tcgen05) products, FP32 accumulate,
                       guard band + exact rescoring                               */
-    RKM_FP8 = 2    /* reserved: FP8 e4m3 products (not built; returns RKM_EINVAL) */
+    RKM_FP8 = 2    /* FP8 e4m3 tensor-core products (users scaled by 2^(8-e) per row,
+                      items per 256-item tile, e = the row's or tile's exponent),
+                      FP32 accumulate, guard band + exact rescoring               */
 } rkm_precision;
 
 typedef struct {

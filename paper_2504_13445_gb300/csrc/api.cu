@@ -88,7 +88,7 @@ struct rkm_ctx {
     // users (original order)
     Buf u_e, u_q, u_n2, u_nrm, u_nhat, u_del, u_pack;
     // items (original order; sorted copies)
-    Buf p_e, p_q, p_n2, p_nrm, p_nhat, p_del, p_perm, p_pack, tmax, thmax, tdel;
+    Buf p_e, p_q, p_n2, p_nrm, p_nhat, p_del, p_perm, p_pack, tmax, thmax, tdel, p_texp;
     // bucket sort scratch
     Buf hist, offs;
     // threshold pass
@@ -104,7 +104,7 @@ struct rkm_ctx {
     unsigned res_off_grid = 0;
     Buf res_U, res_e, res_q, res_tau, res_tid, res_uperm, res_ucum, res_pack, res_meta;
     // query scratch
-    Buf q_e, q_q, q_n2, q_nrm, q_nhat, q_del, q_perm, q_pack, q_tmax, q_thmax, q_tdel, q_cnt;
+    Buf q_e, q_q, q_n2, q_nrm, q_nhat, q_del, q_perm, q_pack, q_tmax, q_thmax, q_tdel, q_cnt, q_texp;
     // host staging for rkm_topn_host
     Buf h_U, h_P, h_ids, h_sc;
     int cand_cap = 0;
@@ -200,6 +200,7 @@ struct rkm_ctx {
                       &tau_tmp, &tid_tmp, &res_U, &res_e, &res_q, &res_tau, &res_tid, &res_uperm, &res_ucum,
                       &res_pack, &res_meta, &q_e, &q_q,
                       &q_n2, &q_nrm, &q_nhat, &q_del, &q_perm, &q_pack, &q_tmax, &q_thmax, &q_tdel, &q_cnt,
+                      &q_texp, &p_texp,
                       &h_U, &h_P, &h_ids, &h_sc};
         for (Buf* b : all) {
             if (b->p) cudaFree(b->p);
@@ -282,9 +283,11 @@ namespace {
 
 // Operand layout of one precision path.
 struct PathShape {
-    bool tc;        // tensor-core kernels
-    int item_tile;  // BI of the product kernels
-    int dp;         // padded depth (elements)
+    bool tc;         // tensor-core kernels
+    bool fp8;        // FP8 e4m3 operands (tensor cores) with power-of-two scales
+    int elem_bytes;  // bytes per packed operand element (4 FP32, 2 BF16, 1 FP8)
+    int item_tile;   // BI of the product kernels
+    int dp;          // padded depth (elements)
     float cacc, eabs;
 };
 
@@ -299,17 +302,31 @@ struct PathShape {
 // accumulation truncates, Fasi, Higham, Mikaitis and Pranesh, PeerJ Comput. Sci. 2021, which
 // needs at most twice gamma_d).  A further d 2^-50 covers the gap between the FP64 reference
 // sum and the exact value for off-grid inputs; eabs covers FP32 underflow of products.
+// FP8 e4m3 products are exact (4-bit significands), but the internal accumulation of
+// kind::f8f6f4 is not documented either; FP8 accumulation on the previous generation kept
+// only about 14 bits (DeepSeek-AI, "DeepSeek-V3 Technical Report", 2024, Section 3.3), so
+// cacc = 2^-8 (64 times that) plus the FP32 term above.  The FP8 representation error
+// (3 mantissa bits, ||x^ - x|| near 2^-5 ||x||) dominates the band anyway.
 PathShape path_shape(rkm_precision prec, int d) {
     PathShape ps{};
     const double dd = (double)d;
     const double g32 = dd * 0x1p-24 / (1.0 - dd * 0x1p-24);
     if (prec == RKM_FP32) {
         ps.tc = false;
+        ps.elem_bytes = 4;
         ps.item_tile = BI_SIMT;
         ps.dp = (int)round_up(d, 32);
         ps.cacc = (float)((2.0 * g32 + dd * 0x1p-50) * (1.0 + 0x1p-20));
+    } else if (prec == RKM_FP8) {
+        ps.tc = true;
+        ps.fp8 = true;
+        ps.elem_bytes = 1;
+        ps.item_tile = BI_TC;
+        ps.dp = (int)round_up(d, 128);
+        ps.cacc = (float)((0x1p-8 + dd * 0x1p-22 + dd * 0x1p-50) * (1.0 + 0x1p-20));
     } else {
         ps.tc = true;
+        ps.elem_bytes = 2;
         ps.item_tile = BI_TC;
         ps.dp = (int)round_up(d, 64);
         ps.cacc = (float)((dd * 0x1p-22 + dd * 0x1p-50) * (1.0 + 0x1p-20));
@@ -330,9 +347,8 @@ rkm_status check_matrix(const float* X, int64_t rows, int64_t ld, int d, const c
 rkm_status check_common(rkm_ctx* c, int d) {
     if (!c) return fail(RKM_EINVAL, "null context");
     if (d < 1 || d > 256) return fail(RKM_EINVAL, "d must be in [1, 256] (got %d)", d);
-    if (c->opts.precision == RKM_FP8) return fail(RKM_EINVAL, "FP8 precision is not built");
-    if (c->opts.precision == RKM_BF16 && !rkm_tc_available())
-        return fail(RKM_EINVAL, "BF16 tensor-core kernels are not built into this library");
+    if (c->opts.precision != RKM_FP32 && !rkm_tc_available())
+        return fail(RKM_EINVAL, "tensor-core kernels are not built into this library");
     CUDA_TRY(cudaSetDevice(c->device));
     return RKM_OK;
 }
@@ -366,8 +382,11 @@ struct RowPrep {
     float* del;   // ||x^ - x|| rounded up
 };
 
+// Users get the norms of their product operand here; items on the FP8 path get them from
+// their pack, whose scale is per item tile (items = true).
 rkm_status prep_rows(rkm_ctx* c, const PathShape& ps, const float* X, int64_t rows, int64_t ld, int d, Buf& be,
-                     Buf& bq, Buf& bn2, Buf& bnrm, Buf& bnhat, Buf& bdel, RowPrep* out, cudaStream_t s) {
+                     Buf& bq, Buf& bn2, Buf& bnrm, Buf& bnhat, Buf& bdel, RowPrep* out, cudaStream_t s,
+                     bool items = false) {
     const int dq = (int)round_up(d, 8);
     TRY(c->ensure(be, rows, &out->e));
     TRY(c->ensure(bq, rows * dq, &out->q));
@@ -375,14 +394,23 @@ rkm_status prep_rows(rkm_ctx* c, const PathShape& ps, const float* X, int64_t ro
     TRY(c->ensure(bnrm, rows, &out->nrm));
     TRY(c->ensure(bnhat, rows, &out->nhat));
     TRY(c->ensure(bdel, rows, &out->del));
-    launch_prep_rows(X, rows, ld, d, out->e, out->q, dq, out->n2, out->nrm, out->nhat, out->del, ps.tc,
-                     &c->st->off_grid, s);
+    const int operand = !ps.tc ? OPERAND_F32 : !ps.fp8 ? OPERAND_BF16 : items ? OPERAND_F32 : OPERAND_FP8_ROW;
+    launch_prep_rows(X, rows, ld, d, out->e, out->q, dq, out->n2, out->nrm, out->nhat, out->del, operand, c->st, s);
     return RKM_OK;
 }
 
+// Operand pack (row perm[r] if perm != null).  FP8: each row scaled by 2^(8 - e) with e its
+// tile's exponent (tile_exp) or its own (row_exp); nhat/del, when given, receive the norms of
+// the descaled operand.
 rkm_status pack(rkm_ctx* c, const PathShape& ps, const float* X, int64_t rows, int64_t ld, int d,
-                const int* perm, int64_t rows_pad, Buf& b, void** out, cudaStream_t s) {
-    if (ps.tc) {
+                const int* perm, int64_t rows_pad, Buf& b, void** out, cudaStream_t s, const int* row_exp = nullptr,
+                const int* tile_exp = nullptr, float* nhat = nullptr, float* del = nullptr) {
+    if (ps.fp8) {
+        uint8_t* p;
+        TRY(c->ensure(b, rows_pad * ps.dp, &p));
+        launch_pack_fp8(X, rows, ld, d, perm, row_exp, tile_exp, ps.item_tile, p, rows_pad, ps.dp, nhat, del, s);
+        *out = p;
+    } else if (ps.tc) {
         __nv_bfloat16* p;
         TRY(c->ensure(b, rows_pad * ps.dp, &p));
         launch_pack_bf16(X, rows, ld, d, perm, p, rows_pad, ps.dp, s);
@@ -399,6 +427,7 @@ rkm_status pack(rkm_ctx* c, const PathShape& ps, const float* X, int64_t rows, i
 // Items: prep, sort by norm (descending), packed sorted operand, tile maxima of the norms.
 struct ItemSide {
     RowPrep rp;
+    int* texp;       // [tiles] FP8 tile exponents (null otherwise)
     int* perm;       // sorted pos -> original id
     void* pack;      // [m_pad][dp]
     float* tmax;     // [tiles] max ||p||
@@ -408,7 +437,7 @@ struct ItemSide {
 };
 
 struct ItemBufs {
-    Buf &e, &q, &n2, &nrm, &nhat, &del, &perm, &pack, &tmax, &thmax, &tdel;
+    Buf &e, &q, &n2, &nrm, &nhat, &del, &perm, &pack, &tmax, &thmax, &tdel, &texp;
 };
 
 rkm_status prep_items(rkm_ctx* c, const PathShape& ps, const float* P, int64_t m, int64_t ldp, int d,
@@ -416,14 +445,20 @@ rkm_status prep_items(rkm_ctx* c, const PathShape& ps, const float* P, int64_t m
     it->m = m;
     it->m_pad = round_up(std::max<int64_t>(m, 1), BI_TC);
     it->tiles = (m + ps.item_tile - 1) / ps.item_tile;
-    TRY(prep_rows(c, ps, P, m, ldp, d, bb.e, bb.q, bb.n2, bb.nrm, bb.nhat, bb.del, &it->rp, s));
+    TRY(prep_rows(c, ps, P, m, ldp, d, bb.e, bb.q, bb.n2, bb.nrm, bb.nhat, bb.del, &it->rp, s, true));
     unsigned *hist, *offs;
     TRY(c->ensure(c->hist, NBUCKET, &hist));
     TRY(c->ensure(c->offs, NBUCKET, &offs));
     TRY(c->ensure(bb.perm, m, &it->perm));
     launch_bucket_sort(it->rp.nrm, m, true, hist, offs, it->perm, nullptr, s);
-    TRY(pack(c, ps, P, m, ldp, d, it->perm, it->m_pad, bb.pack, &it->pack, s));
     const int64_t nt = std::max<int64_t>(it->tiles, 1);
+    it->texp = nullptr;
+    if (ps.fp8) {
+        TRY(c->ensure(bb.texp, nt, &it->texp));
+        launch_tile_exp(it->rp.e, it->perm, m, ps.item_tile, it->tiles, it->texp, s);
+    }
+    TRY(pack(c, ps, P, m, ldp, d, it->perm, it->m_pad, bb.pack, &it->pack, s, nullptr, it->texp, it->rp.nhat,
+             it->rp.del));
     TRY(c->ensure(bb.tmax, nt, &it->tmax));
     TRY(c->ensure(bb.thmax, nt, &it->thmax));
     TRY(c->ensure(bb.tdel, nt, &it->tdel));
@@ -434,12 +469,12 @@ rkm_status prep_items(rkm_ctx* c, const PathShape& ps, const float* P, int64_t m
 
 ItemBufs catalogue_bufs(rkm_ctx* c) {
     return ItemBufs{c->p_e, c->p_q, c->p_n2, c->p_nrm, c->p_nhat, c->p_del, c->p_perm, c->p_pack, c->tmax,
-                    c->thmax, c->tdel};
+                    c->thmax, c->tdel, c->p_texp};
 }
 
 ItemBufs query_bufs(rkm_ctx* c) {
     return ItemBufs{c->q_e, c->q_q, c->q_n2, c->q_nrm, c->q_nhat, c->q_del, c->q_perm, c->q_pack, c->q_tmax,
-                    c->q_thmax, c->q_tdel};
+                    c->q_thmax, c->q_tdel, c->q_texp};
 }
 
 // Threshold pass of one problem, split so that a batch can put many problems into one
@@ -462,7 +497,7 @@ rkm_status threshold_prepare(rkm_ctx* c, const PathShape& ps, const float* U, in
     pl->n_pad = round_up(std::max<int64_t>(n, 1), BU);
     {
         Phase ph(c, s, RKM_PHASE_PREP);
-        TRY(pack(c, ps, U, n, ldu, d, nullptr, pl->n_pad, c->u_pack, &pl->apack, s));
+        TRY(pack(c, ps, U, n, ldu, d, nullptr, pl->n_pad, c->u_pack, &pl->apack, s, up.e));
     }
     pl->cap = c->cand_cap;
     pl->nseg = ps.tc ? 2 : 1;
@@ -490,6 +525,8 @@ rkm_status threshold_prepare(rkm_ctx* c, const PathShape& ps, const float* U, in
     a.tdel = it.tdel;
     a.cacc = ps.cacc;
     a.eabs = ps.eabs;
+    a.uexp = up.e;
+    a.texp = it.texp;
     a.cand = pl->cand;
     a.cand_cnt = pl->cand_cnt;
     a.lfin_key = pl->lfin;
@@ -501,7 +538,7 @@ rkm_status threshold_prepare(rkm_ctx* c, const PathShape& ps, const float* U, in
 
 rkm_status threshold_descriptor(const PathShape& ps, const ThrPlan& pl, const ItemSide& it, TcInstance* out) {
     TmapPair tm;
-    TRY(make_tmaps(pl.apack, pl.n_pad, it.pack, it.m_pad, ps.dp, BI_TC, &tm));
+    TRY(make_tmaps(pl.apack, pl.n_pad, it.pack, it.m_pad, ps.dp, BI_TC, ps.elem_bytes, &tm));
     out->tmA = tm.a;
     out->tmB = tm.b;
     out->a = pl.a;
@@ -519,7 +556,7 @@ rkm_status threshold_launch_one(rkm_ctx* c, const PathShape& ps, const ThrPlan& 
         TRY(c->instances(1, &hi, &di));
         TRY(threshold_descriptor(ps, pl, it, hi));
         CUDA_TRY(cudaMemcpyAsync(di, hi, sizeof(TcInstance), cudaMemcpyHostToDevice, s));
-        launch_threshold_tc(di, 1, (pl.a.n + BU - 1) / BU, pl.a.k, ps.dp, c->num_sms, s);
+        launch_threshold_tc(di, 1, (pl.a.n + BU - 1) / BU, pl.a.k, ps.dp, ps.fp8, c->num_sms, s);
     } else {
         launch_threshold_simt(pl.a, s);
     }
@@ -595,9 +632,9 @@ rkm_status order_users(rkm_ctx* c, const PathShape& ps, const float* U, int64_t 
     launch_user_ratio(tau, up.n2, n, r, s);
     launch_bucket_sort(r, n, false, hist, offs, uo->uperm, uo->ucum, s);
     const int64_t n_pad = round_up(std::max<int64_t>(n, 1), BU);
-    TRY(pack(c, ps, U, n, ldu, d, uo->uperm, n_pad, bb.pack, &uo->pack, s));
+    TRY(pack(c, ps, U, n, ldu, d, uo->uperm, n_pad, bb.pack, &uo->pack, s, up.e));
     TRY(c->ensure(bb.meta, n, &uo->meta));
-    launch_user_meta(tau, up.nrm, up.nhat, up.del, uo->uperm, n, uo->meta, s);
+    launch_user_meta(tau, up.nrm, up.nhat, up.del, up.e, uo->uperm, n, uo->meta, s);
     return RKM_OK;
 }
 
@@ -625,6 +662,7 @@ rkm_status count_stage(rkm_ctx* c, const PathShape& ps, int64_t n, const UserOrd
     a.tmax = it.tmax;
     a.thmax = it.thmax;
     a.tdel = it.tdel;
+    a.texp = it.texp;
     a.nprefix = nprefix;
     a.unit_off = unit_off;
     a.t_begin = t_begin;
@@ -639,8 +677,8 @@ rkm_status count_stage(rkm_ctx* c, const PathShape& ps, int64_t n, const UserOrd
     if (ps.tc) {
         TmapPair tm;
         const int64_t n_pad = round_up(std::max<int64_t>(n, 1), BU);
-        TRY(make_tmaps(uo.pack, n_pad, it.pack, it.m_pad, ps.dp, BI_TC, &tm));
-        launch_count_tc(a, &tm.a, &tm.b, s);
+        TRY(make_tmaps(uo.pack, n_pad, it.pack, it.m_pad, ps.dp, BI_TC, ps.elem_bytes, &tm));
+        launch_count_tc(a, &tm.a, &tm.b, ps.fp8, s);
     } else {
         launch_count_simt(a, s);
     }
@@ -1065,7 +1103,7 @@ rkm_status rkm_item_bounds(rkm_ctx* c, const float* U, int64_t n, int64_t ldu, c
     RowPrep up, pp;
     const PathShape ps = path_shape(c->opts.precision, d);
     TRY(prep_rows(c, ps, U, n, ldu, d, c->u_e, c->u_q, c->u_n2, c->u_nrm, c->u_nhat, c->u_del, &up, s));
-    TRY(prep_rows(c, ps, P, m, ldp, d, c->p_e, c->p_q, c->p_n2, c->p_nrm, c->p_nhat, c->p_del, &pp, s));
+    TRY(prep_rows(c, ps, P, m, ldp, d, c->p_e, c->p_q, c->p_n2, c->p_nrm, c->p_nhat, c->p_del, &pp, s, true));
     float* r;
     unsigned *hist, *offs, *ucum;
     int* uperm;
@@ -1223,7 +1261,7 @@ rkm_status batch_enqueue(rkm_ctx* c, const rkm_instance* inst, int count, cudaSt
             max_dp = std::max(max_dp, w[i].ps.dp);
         }
         CUDA_TRY(cudaMemcpyAsync(dev, c->batch_host, (size_t)count * sizeof(TcInstance), cudaMemcpyHostToDevice, s));
-        launch_threshold_tc(dev, count, units, kheap, max_dp, c->num_sms, s);
+        launch_threshold_tc(dev, count, units, kheap, max_dp, w[0].ps.fp8, c->num_sms, s);
     } else {
         for (int i = 0; i < count; ++i) launch_threshold_simt(w[i].pl.a, s);
     }

@@ -40,7 +40,8 @@ struct DevStatus {
 struct __align__(16) UserMeta {
     float tau_hi, tau_lo, un, unh, ud;
     int uorig;
-    float pad0, pad1;
+    int uexp;  // row exponent e (max|u| <= 2^e); scales the FP8 operand
+    float pad1;
 };
 
 // Candidate of the threshold pass: an upper bound of u.p and the item's sorted position.
@@ -93,6 +94,13 @@ __device__ __forceinline__ float err_bound(float cacc, float eabs, float un, flo
     const float rep = __fadd_ru(__fmul_ru(udel, pnhat), __fmul_ru(un, pdel));
     return __fadd_ru(__fadd_ru(rep, __fmul_ru(cacc, __fmul_ru(unhat, pnhat))), eabs);
 }
+
+// Exponent of the FP8 operand scale 2^(8 - e) of a row (or tile) with max|x| <= 2^e, clamped
+// to [-60, 60] so that the scale, the descaled operand and the product factor
+// 2^(e_u + e_T - 16) are exact FP32 powers of two.  Rows outside that range saturate (at
+// 448) or underflow in FP8; the norms ||x^ - x|| of the actual rounding carry that error
+// into the guard band, so results stay exact.
+__host__ __device__ __forceinline__ int fp8_exp(int e) { return e < -60 ? -60 : (e > 60 ? 60 : e); }
 
 // Three-input maximum (sm_100 and later).
 __device__ __forceinline__ float fmax3f(float a, float b, float c) {

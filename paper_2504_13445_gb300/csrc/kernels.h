@@ -21,13 +21,31 @@ inline void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); 
 // ---- prep.cu (K1 prep, K4 bounds and the bucket sort) ------------------------------
 
 // Per row: exponent e (max|x| <= 2^e), integer grid codes q = x * 2^(12-e) (int16,
-// row stride dq), exact/upper-bound squared norm, ||x|| rounded up; *grid_flag is set to 1
+// row stride dq), exact/upper-bound squared norm, ||x|| rounded up; st->off_grid is set
 // when a row is not on the grid.
 // Also ||x^|| and ||x^ - x|| (rounded up) of the operand x^ the product kernels see:
-// x^ = BF16 round-to-nearest of x when round_bf16, else x itself.
+// OPERAND_F32: x itself; OPERAND_BF16: BF16 round-to-nearest of x; OPERAND_FP8_ROW: x scaled
+// by 2^(8-e), rounded to FP8 e4m3 (nearest even) and scaled back (per-row scale).  Operands
+// with a per-tile scale get their norms from launch_pack_fp8 instead.
+enum OperandKind { OPERAND_F32 = 0, OPERAND_BF16 = 1, OPERAND_FP8_ROW = 2 };
 void launch_prep_rows(const float* X, int64_t rows, int64_t ld, int d, int* ex, int16_t* q,
                       int dq, double* norm2, float* nrm_hi, float* nhat_hi, float* del_hi,
-                      bool round_bf16, unsigned* grid_flag, cudaStream_t s);
+                      int operand, DevStatus* st, cudaStream_t s);
+
+// FP8 e4m3 operand copy dst[r][c] (rows_pad x dp bytes) of X (row perm[r] if perm != null):
+// row r holds e4m3(x * 2^(8 - e_r)) with e_r = tile_exp[r / tile] when tile_exp != null,
+// else fp8_exp(row_exp[src]) (the row's own exponent).  Since max|x| <= 2^e, scaled values
+// stay within +-256 (e4m3 saturates at 448) unless the exponent was clamped.  When
+// nhat/del are non-null, also writes ||x^|| and ||x^ - x|| (rounded up) of the descaled
+// operand at the source row.
+void launch_pack_fp8(const float* X, int64_t rows, int64_t ld, int d, const int* perm, const int* row_exp,
+                     const int* tile_exp, int tile, uint8_t* dst, int64_t rows_pad, int dp, float* nhat,
+                     float* del, cudaStream_t s);
+
+// Per tile of `tile` consecutive sorted rows: fp8_exp of the largest row exponent ex[perm[i]]
+// (0 for an empty tile).
+void launch_tile_exp(const int* ex, const int* perm, int64_t count, int tile, int64_t tiles, int* texp,
+                     cudaStream_t s);
 
 // Zero-padded operand copy dst[r][c] (rows_pad x dp) of X (row perm[r] if perm != null).
 void launch_pack_f32(const float* X, int64_t rows, int64_t ld, int d, const int* perm,
@@ -55,8 +73,8 @@ void launch_tile_max(const float* nrm, const float* nhat, const float* del, cons
 void launch_user_ratio(const double* tau, const double* norm2, int64_t n, float* r, cudaStream_t s);
 
 // K4: per-user records of the counting pass, in ratio order (perm: ratio order -> user).
-void launch_user_meta(const double* tau, const float* nrm, const float* nhat, const float* del, const int* perm,
-                      int64_t n, UserMeta* meta, cudaStream_t s);
+void launch_user_meta(const double* tau, const float* nrm, const float* nhat, const float* del, const int* ex,
+                      const int* perm, int64_t n, UserMeta* meta, cudaStream_t s);
 
 // K4: uscore[i] = number of users whose ratio bucket <= bucket(||p_i||) (ucum lookup).
 void launch_item_uscore(const float* nrm_hi, int64_t m, const unsigned* ucum, int* uscore,
@@ -76,6 +94,8 @@ struct ThresholdArgs {
     const float* thmax;   // [item tiles] max ||p^||
     const float* tdel;    // [item tiles] max ||p^ - p||
     float cacc, eabs;     // accumulation coefficient and absolute (underflow) term of the bound
+    const int* uexp;      // [n] FP8: user row exponents (operand scale 2^(8-e)); else unused
+    const int* texp;      // [item tiles] FP8: item tile exponents; else unused
     Cand* cand;           // [n][nseg][cap]
     int* cand_cnt;        // [n][nseg]
     unsigned* lfin_key;   // [n] float_key of the final lower threshold L_u (atomic max; 0 = none)
@@ -95,9 +115,10 @@ struct __align__(64) TcInstance {
 };
 // Tensor-core threshold pass over `count` instances in one persistent launch.  inst: device
 // array; total_units = sum of the instances' user tiles; kheap = largest k; max_dp = largest
-// padded depth.
+// padded depth (elements).  fp8: operands are e4m3 (128 per K-block) with power-of-two
+// scales, else BF16 (64 per K-block); every instance of a launch has the same kind.
 void launch_threshold_tc(const TcInstance* inst, int count, long long total_units, int kheap, int max_dp,
-                         int num_sms, cudaStream_t s);
+                         bool fp8, int num_sms, cudaStream_t s);
 
 // ---- exact rescoring (K3, K6, K8) ---------------------------------------------------
 
@@ -139,6 +160,7 @@ struct CountArgs {
     const float* tmax;      // per item tile: max ||p||
     const float* thmax;     // per item tile: max ||p^||
     const float* tdel;      // per item tile: max ||p^ - p||
+    const int* texp;        // per item tile: FP8 tile exponent (unused for BF16 / FP32)
     const int* nprefix;     // per item tile: users needed (ratio-order prefix length)
     const unsigned* unit_off;  // [tiles+1] work units per item tile, exclusive scan
     int t_begin;            // first item tile of the stage
@@ -154,7 +176,7 @@ void launch_build_units(const float* tmax, const unsigned* ucum, int t_begin, in
                         const int* t_end_dev, int tile_users, int group, int* nprefix,
                         unsigned* unit_off, DevStatus* st, cudaStream_t s);
 void launch_count_simt(const CountArgs& a, cudaStream_t s);
-void launch_count_tc(const CountArgs& a, const void* tmapA, const void* tmapB, cudaStream_t s);
+void launch_count_tc(const CountArgs& a, const void* tmapA, const void* tmapB, bool fp8, cudaStream_t s);
 
 // ---- top-N (K7) ---------------------------------------------------------------------
 

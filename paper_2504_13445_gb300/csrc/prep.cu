@@ -5,6 +5,7 @@
 // exact rescoring and zero-padded operand copies for the product kernels.
 #include <cuda_runtime.h>
 #include <cuda_bf16.h>
+#include <cuda_fp8.h>
 #include <math.h>
 
 #include "common.cuh"
@@ -13,6 +14,16 @@
 namespace rkm {
 
 namespace {
+
+// x^ of the FP8 operand with scale 2^(8-e) (e already clamped by fp8_exp): e4m3
+// round-to-nearest-even (saturating at 448) of x * 2^(8-e), as a float; descaled by the
+// caller (exact in FP32).
+__device__ __forceinline__ float fp8_scaled(float v, int e, __nv_fp8_storage_t* code) {
+    const __nv_fp8_storage_t c = __nv_cvt_float_to_fp8(ldexpf(v, 8 - e), __NV_SATFINITE, __NV_E4M3);
+    if (code) *code = c;
+    const __half_raw h = __nv_cvt_fp8_to_halfraw(c, __NV_E4M3);
+    return __half2float(__half(h));
+}
 
 inline int grid_for(int64_t work, int per_block, int cap = 1 << 20) {
     int64_t g = (work + per_block - 1) / per_block;
@@ -26,7 +37,7 @@ inline int grid_for(int64_t work, int per_block, int cap = 1 << 20) {
 __global__ void k_prep_rows(const float* __restrict__ X, int64_t rows, int64_t ld, int d,
                             int* __restrict__ ex, int16_t* __restrict__ q, int dq,
                             double* __restrict__ norm2, float* __restrict__ nrm_hi,
-                            float* __restrict__ nhat_hi, float* __restrict__ del_hi, int round_bf16,
+                            float* __restrict__ nhat_hi, float* __restrict__ del_hi, int operand,
                             unsigned* grid_flag) {
     const int lane = threadIdx.x & 31;
     const int64_t warps = ((int64_t)gridDim.x * blockDim.x) >> 5;
@@ -55,7 +66,9 @@ __global__ void k_prep_rows(const float* __restrict__ X, int64_t rows, int64_t l
             s2 += (long long)qi * qi;
             d2 = __fmaf_ru(v, v, d2);
             // Operand the product kernels see, and its rounding error (exact in FP32).
-            const float vh = round_bf16 ? __bfloat162float(__float2bfloat16_rn(v)) : v;
+            float vh = v;
+            if (operand == OPERAND_BF16) vh = __bfloat162float(__float2bfloat16_rn(v));
+            if (operand == OPERAND_FP8_ROW) vh = ldexpf(fp8_scaled(v, fp8_exp(e), nullptr), fp8_exp(e) - 8);
             const float dv = vh - v;
             h2 = __fmaf_ru(vh, vh, h2);
             e2 = __fmaf_ru(dv, dv, e2);
@@ -108,6 +121,63 @@ __global__ void k_pack(const float* __restrict__ X, int64_t rows, int64_t ld, in
             v = X[src * ld + c];
         }
         dst[idx] = cvt_from_float<T>(v);
+    }
+}
+
+// One warp per packed row: e4m3 codes of the row scaled by 2^(8 - e) (e = its tile's or its
+// own exponent), zero padding, and the norms of the descaled operand at the source row.
+__global__ void k_pack_fp8(const float* __restrict__ X, int64_t rows, int64_t ld, int d,
+                           const int* __restrict__ perm, const int* __restrict__ row_exp,
+                           const int* __restrict__ tile_exp, int tile, uint8_t* __restrict__ dst, int64_t rows_pad,
+                           int dp, float* __restrict__ nhat, float* __restrict__ del) {
+    const int lane = threadIdx.x & 31;
+    const int64_t warps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t r = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; r < rows_pad; r += warps) {
+        uint8_t* out = dst + r * dp;
+        if (r >= rows) {
+            for (int c = lane; c < dp; c += 32) out[c] = 0;
+            continue;
+        }
+        const int64_t src = perm ? (int64_t)perm[r] : r;
+        const int e = tile_exp ? tile_exp[r / tile] : fp8_exp(row_exp[src]);
+        const float* x = X + src * ld;
+        float h2 = 0.f, e2 = 0.f;
+        for (int c = lane; c < dp; c += 32) {
+            __nv_fp8_storage_t code = 0;
+            if (c < d) {
+                const float v = x[c];
+                const float vh = ldexpf(fp8_scaled(v, e, &code), e - 8);
+                const float dv = vh - v;
+                h2 = __fmaf_ru(vh, vh, h2);
+                e2 = __fmaf_ru(dv, dv, e2);
+            }
+            out[c] = (uint8_t)code;
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            h2 = __fadd_ru(h2, __shfl_xor_sync(0xffffffffu, h2, o));
+            e2 = __fadd_ru(e2, __shfl_xor_sync(0xffffffffu, e2, o));
+        }
+        if (lane == 0) {
+            if (nhat) nhat[src] = __fsqrt_ru(h2);
+            if (del) del[src] = __fsqrt_ru(e2);
+        }
+    }
+}
+
+// Largest row exponent of each tile of sorted rows.
+__global__ void k_tile_exp(const int* __restrict__ ex, const int* __restrict__ perm, int64_t count, int tile,
+                           int64_t tiles, int* __restrict__ texp) {
+    const int lane = threadIdx.x & 31;
+    const int64_t warps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t t = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; t < tiles; t += warps) {
+        int mx = INT_MIN;
+        int64_t i0 = t * tile, i1 = i0 + tile;
+        if (i1 > count) i1 = count;
+        for (int64_t i = i0 + lane; i < i1; i += 32) mx = max(mx, ex[perm[i]]);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+        if (lane == 0) texp[t] = (mx == INT_MIN) ? 0 : fp8_exp(mx);
     }
 }
 
@@ -213,7 +283,8 @@ __global__ void k_user_ratio(const double* __restrict__ tau, const double* __res
 
 __global__ void k_user_meta(const double* __restrict__ tau, const float* __restrict__ nrm,
                             const float* __restrict__ nhat, const float* __restrict__ del,
-                            const int* __restrict__ perm, int64_t n, UserMeta* __restrict__ meta) {
+                            const int* __restrict__ ex, const int* __restrict__ perm, int64_t n,
+                            UserMeta* __restrict__ meta) {
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
         const int u = perm[i];
         const double t = tau[u];
@@ -224,7 +295,7 @@ __global__ void k_user_meta(const double* __restrict__ tau, const float* __restr
         r.unh = nhat[u];
         r.ud = del[u];
         r.uorig = u;
-        r.pad0 = 0.f;
+        r.uexp = ex[u];
         r.pad1 = 0.f;
         meta[i] = r;
     }
@@ -240,13 +311,29 @@ __global__ void k_item_uscore(const float* __restrict__ nrm_hi, int64_t m,
 }  // namespace
 
 void launch_prep_rows(const float* X, int64_t rows, int64_t ld, int d, int* ex, int16_t* q, int dq,
-                      double* norm2, float* nrm_hi, float* nhat_hi, float* del_hi, bool round_bf16,
-                      unsigned* grid_flag, cudaStream_t s) {
+                      double* norm2, float* nrm_hi, float* nhat_hi, float* del_hi, int operand,
+                      DevStatus* st, cudaStream_t s) {
     if (rows <= 0) return;
     note_launch();
     k_prep_rows<<<grid_for(rows * 32, 256, 65536), 256, 0, s>>>(X, rows, ld, d, ex, q, dq, norm2,
-                                                                 nrm_hi, nhat_hi, del_hi, round_bf16 ? 1 : 0,
-                                                                 grid_flag);
+                                                                 nrm_hi, nhat_hi, del_hi, operand,
+                                                                 &st->off_grid);
+}
+
+void launch_pack_fp8(const float* X, int64_t rows, int64_t ld, int d, const int* perm, const int* row_exp,
+                     const int* tile_exp, int tile, uint8_t* dst, int64_t rows_pad, int dp, float* nhat,
+                     float* del, cudaStream_t s) {
+    if (rows_pad <= 0) return;
+    note_launch();
+    k_pack_fp8<<<grid_for(rows_pad * 32, 256, 65536), 256, 0, s>>>(X, rows, ld, d, perm, row_exp, tile_exp, tile,
+                                                                     dst, rows_pad, dp, nhat, del);
+}
+
+void launch_tile_exp(const int* ex, const int* perm, int64_t count, int tile, int64_t tiles, int* texp,
+                     cudaStream_t s) {
+    if (tiles <= 0) return;
+    note_launch();
+    k_tile_exp<<<grid_for(tiles * 32, 256, 65536), 256, 0, s>>>(ex, perm, count, tile, tiles, texp);
 }
 
 void launch_pack_f32(const float* X, int64_t rows, int64_t ld, int d, const int* perm, float* dst,
@@ -315,11 +402,11 @@ void launch_user_ratio(const double* tau, const double* norm2, int64_t n, float*
     }
 }
 
-void launch_user_meta(const double* tau, const float* nrm, const float* nhat, const float* del, const int* perm,
-                      int64_t n, UserMeta* meta, cudaStream_t s) {
+void launch_user_meta(const double* tau, const float* nrm, const float* nhat, const float* del, const int* ex,
+                      const int* perm, int64_t n, UserMeta* meta, cudaStream_t s) {
     if (n > 0) {
         note_launch();
-        k_user_meta<<<grid_for(n, 256, 65536), 256, 0, s>>>(tau, nrm, nhat, del, perm, n, meta);
+        k_user_meta<<<grid_for(n, 256, 65536), 256, 0, s>>>(tau, nrm, nhat, del, ex, perm, n, meta);
     }
 }
 

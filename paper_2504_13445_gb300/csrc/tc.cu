@@ -1,6 +1,7 @@
 // Tensor-core (tcgen05) product kernels of the threshold pass (K2) and the counting
-// pass (K5): BF16 operands staged by TMA into 128-byte-swizzled shared memory, one
-// thread issuing 128 x 256 x 16 MMAs into a double-buffered FP32 accumulator in TMEM
+// pass (K5): BF16 or FP8 e4m3 operands staged by TMA into 128-byte-swizzled shared memory
+// (a K-block is 128 bytes of every row: 64 BF16 or 128 FP8 values), one thread issuing
+// 128 x 256 x 16 (BF16) or 128 x 256 x 32 (FP8) MMAs into a double-buffered FP32 accumulator in TMEM
 // (2 x 256 columns), and eight epilogue warps that read the accumulator back with
 // tcgen05.ld and run the per-user epilogues of epilogue.cuh.  The user x item product
 // never leaves the SM.
@@ -32,7 +33,7 @@ namespace {
 constexpr int TC_THREADS = 320;
 constexpr int MAX_SLOTS = 4;
 constexpr uint32_t TMEM_COLS = 512;
-constexpr uint32_t KB_BYTES_U = 128 * 128;  // one K-block (64 BF16) of 128 user rows
+constexpr uint32_t KB_BYTES_U = 128 * 128;  // one K-block (128 bytes: 64 BF16 / 128 FP8) of 128 user rows
 constexpr uint32_t KB_BYTES_I = 256 * 128;  // one K-block of 256 item rows
 constexpr int SMEM_LIMIT = 232448;          // 227 KB opt-in maximum per block
 
@@ -50,6 +51,29 @@ struct TcLayout {
     int slots;                       // ring slots
     int nres;                        // resident-operand buffers (2 = next unit loads during this one)
 };
+
+// Values per 128-byte K-block row and the MMA of the operand kind.
+template <bool FP8>
+struct Operand {
+    static constexpr int KELEMS = FP8 ? 128 : 64;
+    static constexpr int KSHIFT = FP8 ? 7 : 6;
+    static __device__ __forceinline__ uint32_t idesc() { return FP8 ? idesc_e4m3_f32(BU, BI_TC) : idesc_bf16_f32(BU, BI_TC); }
+    static __device__ __forceinline__ void mma(uint32_t d, uint64_t ad, uint64_t bd, uint32_t id, uint32_t acc) {
+        if constexpr (FP8) tc_mma_f8(d, ad, bd, id, acc);
+        else tc_mma_bf16(d, ad, bd, id, acc);
+    }
+};
+
+// 2^k as a float (exact; subnormal below 2^-126).  FP8 operands carry the scales 2^(8-e_u)
+// and 2^(8-e_T), so an accumulator times 2^(e_u + e_T - 16) is the product of the descaled
+// operands; fp8_exp limits the exponents to [-60, 60], so k stays within [-136, 104].
+__device__ __forceinline__ float pow2i(int k) { return k >= -126 ? __int_as_float((k + 127) << 23) : ldexpf(1.f, k); }
+
+template <int N>
+__device__ __forceinline__ void scale_values(float (&v)[N], float f) {
+#pragma unroll
+    for (int j = 0; j < N; ++j) v[j] *= f;
+}
 
 __device__ __forceinline__ uint8_t* align1024(uint8_t* raw) {
     const uint32_t a = smem_u32(raw);
@@ -121,9 +145,11 @@ __device__ __forceinline__ int unit_instance(const TcInstance* inst, int count, 
 // tile) pairs numbered consecutively across the instances; CTA b takes units b, b + grid, ...
 // A unit streams every item tile of its instance, so the caller orders the instances by
 // descending cost to balance the CTAs.
+template <bool FP8>
 __global__ void __launch_bounds__(TC_THREADS, 1)
     k_threshold_tc(const TcInstance* __restrict__ inst, int count, long long total_units, int kheap,
                    const TcLayout L) {
+    using Op = Operand<FP8>;
     extern __shared__ uint8_t smem_raw[];
     uint8_t* sm = align1024(smem_raw);
     uint8_t* sA = sm + L.res_off;
@@ -153,7 +179,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             for (long long w = blockIdx.x; w < total_units && ok; w += gridDim.x) {
                 const TcInstance& I = inst[unit_instance(inst, count, w)];
                 st = I.a.st;
-                const int KB = I.a.dp >> 6;
+                const int KB = I.a.dp >> Op::KSHIFT;
                 const long long ut = w - I.unit_begin;
                 const int item_tiles = (int)((I.a.m + BI_TC - 1) / BI_TC);
                 const int rb = res_loads % L.nres, ru = res_loads / L.nres;
@@ -161,7 +187,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                 uint8_t* dst = sA + rb * L.res_bytes;
                 mbar_expect_tx(&B->res_full[rb], KB * KB_BYTES_U);
                 for (int kb = 0; kb < KB; ++kb)
-                    tma_load_2d(dst + kb * KB_BYTES_U, &I.tmA, &B->res_full[rb], kb * 64, (int)(ut * BU));
+                    tma_load_2d(dst + kb * KB_BYTES_U, &I.tmA, &B->res_full[rb], kb * Op::KELEMS, (int)(ut * BU));
                 ++res_loads;
                 for (int it = 0; it < item_tiles && ok; ++it) {
                     for (int kb = 0; kb < KB; ++kb) {
@@ -170,7 +196,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                             break;
                         }
                         mbar_expect_tx(&B->full[slot], KB_BYTES_I);
-                        tma_load_2d(ring + slot * KB_BYTES_I, &I.tmB, &B->full[slot], kb * 64, it * BI_TC);
+                        tma_load_2d(ring + slot * KB_BYTES_I, &I.tmB, &B->full[slot], kb * Op::KELEMS, it * BI_TC);
                         ++issued[slot];
                         if (++slot == S) {
                             slot = 0;
@@ -189,7 +215,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         }
     } else if (warp == 1) {
         if (lane == 0) {
-            const uint32_t idesc = idesc_bf16_f32(BU, BI_TC);
+            const uint32_t idesc = Op::idesc();
             int slot = 0;
             uint32_t ph = 0, tile_j = 0;
             int iter = 0;
@@ -198,7 +224,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             for (long long w = blockIdx.x; w < total_units && ok; w += gridDim.x, ++iter) {
                 const TcInstance& I = inst[unit_instance(inst, count, w)];
                 st = I.a.st;
-                const int KB = I.a.dp >> 6;
+                const int KB = I.a.dp >> Op::KSHIFT;
                 const int item_tiles = (int)((I.a.m + BI_TC - 1) / BI_TC);
                 const int rb = iter % L.nres;
                 if (!mbar_wait(&B->res_full[rb], (iter / L.nres) & 1, abort, st)) break;
@@ -222,7 +248,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                         const uint64_t bd = sdesc_sw128(smem_u32(ring + slot * KB_BYTES_I));
 #pragma unroll
                         for (int k = 0; k < 4; ++k)
-                            tc_mma_bf16(d, ad + 2u * k, bd + 2u * k, idesc, (kb | k) != 0 ? 1u : 0u);
+                            Op::mma(d, ad + 2u * k, bd + 2u * k, idesc, (kb | k) != 0 ? 1u : 0u);
                         tc_commit(&B->empty[slot]);
                         if (++slot == S) {
                             slot = 0;
@@ -268,6 +294,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             const float un = active ? a.unrm[u] : 0.f;
             const float unh = active ? a.unhat[u] : 0.f;
             const float ud = active ? a.udel[u] : 0.f;
+            const int ue = (FP8 && active) ? fp8_exp(a.uexp[u]) : 0;
             Cand* mycand = a.cand + ((active ? u : 0) * a.nseg + h) * (int64_t)a.cap;
             // This group's first tile of the unit, then every other one: the bound maxima of
             // the next one are loaded while the current one is processed.
@@ -293,6 +320,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                 __syncwarp();
                 tc_fence_after();
                 const float E = err_bound(a.cacc, a.eabs, un, unh, ud, thm, tdl);
+                const float f = FP8 ? pow2i(ue + a.texp[it] - 16) : 1.f;  // descale of the FP8 product
                 // The partner's bound may be stale or from this unit's start (-inf):
                 // any value it held is a valid lower bound of tau_u for the current user.
                 s.Lx = read_bound(&Lpub[(1 - h) * BU + r], (unsigned)w);
@@ -306,6 +334,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                         auto load = [&](int c0, float (&v)[32]) {
                             __syncwarp();
                             tmem_ld32(tb + c0, v);
+                            if constexpr (FP8) scale_values(v, f);
                         };
                         const float lw = warm_bound<32, BI_TC>(load, it * BI_TC, a.m, a.k, E);
                         s.Lw = active ? lw : -INFINITY;
@@ -325,6 +354,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                     {
                         float v[32];
                         as_floats(ra, v);
+                        if constexpr (FP8) scale_values(v, f);
                         sel_chunk(v, active, it * BI_TC + c0, a.m, E, s, mycand, a.cap, heap, r, a.k, a.st);
                     }
                     __syncwarp();
@@ -333,6 +363,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                     {
                         float v[32];
                         as_floats(rb, v);
+                        if constexpr (FP8) scale_values(v, f);
                         sel_chunk(v, active, it * BI_TC + c0 + 32, a.m, E, s, mycand, a.cap, heap, r, a.k, a.st);
                     }
                     __syncwarp();
@@ -412,9 +443,11 @@ __device__ __forceinline__ void flush_counts(int* cw, int lane, int pos0, int64_
     __syncwarp();
 }
 
+template <bool FP8>
 __global__ void __launch_bounds__(TC_THREADS, 1)
     k_count_tc(const CountArgs a, const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
                const TcLayout L) {
+    using Op = Operand<FP8>;
     extern __shared__ uint8_t smem_raw[];
     uint8_t* sm = align1024(smem_raw);
     uint8_t* sB = sm + L.res_off;
@@ -422,7 +455,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     int* cnt_all = reinterpret_cast<int*>(sm + L.aux_off);
     TcBars* B = reinterpret_cast<TcBars*>(sm + L.bar_off);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int KB = a.dp >> 6;
+    const int KB = a.dp >> Op::KSHIFT;
     const int S = L.slots;
     const unsigned total = a.st->units_total;
     const int len = a.st->t_end - a.t_begin;
@@ -450,7 +483,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                 uint8_t* dst = sB + rb * L.res_bytes;
                 mbar_expect_tx(&B->res_full[rb], KB * KB_BYTES_I);
                 for (int kb = 0; kb < KB; ++kb)
-                    tma_load_2d(dst + kb * KB_BYTES_I, &tmB, &B->res_full[rb], kb * 64, T * BI_TC);
+                    tma_load_2d(dst + kb * KB_BYTES_I, &tmB, &B->res_full[rb], kb * Op::KELEMS, T * BI_TC);
                 ++res_loads;
                 for (int64_t ut = ut0; ut < ut1 && ok; ++ut) {
                     for (int kb = 0; kb < KB; ++kb) {
@@ -459,7 +492,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                             break;
                         }
                         mbar_expect_tx(&B->full[slot], KB_BYTES_U);
-                        tma_load_2d(ring + slot * KB_BYTES_U, &tmA, &B->full[slot], kb * 64, (int)(ut * BU));
+                        tma_load_2d(ring + slot * KB_BYTES_U, &tmA, &B->full[slot], kb * Op::KELEMS, (int)(ut * BU));
                         ++issued[slot];
                         if (++slot == S) {
                             slot = 0;
@@ -480,7 +513,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         }
     } else if (warp == 1) {
         if (lane == 0) {
-            const uint32_t idesc = idesc_bf16_f32(BU, BI_TC);
+            const uint32_t idesc = Op::idesc();
             int slot = 0;
             uint32_t ph = 0, tile_j = 0;
             int iter = 0;
@@ -511,7 +544,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                         const uint64_t bd = sdesc_sw128(smem_u32(sBr + kb * KB_BYTES_I));
 #pragma unroll
                         for (int k = 0; k < 4; ++k)
-                            tc_mma_bf16(d, ad + 2u * k, bd + 2u * k, idesc, (kb | k) != 0 ? 1u : 0u);
+                            Op::mma(d, ad + 2u * k, bd + 2u * k, idesc, (kb | k) != 0 ? 1u : 0u);
                         tc_commit(&B->empty[slot]);
                         if (++slot == S) {
                             slot = 0;
@@ -550,6 +583,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         uint32_t use = 0;
         int curT = -1;
         float pnh = 0.f, pd = 0.f;
+        int te = 0;
         while (cur.valid) {
             if (nxt.valid && nxt.ut * BU + r < a.n) um_nxt = a.meta[nxt.ut * BU + r];
             if (cur.T != curT) {
@@ -557,6 +591,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                 curT = cur.T;
                 pnh = a.thmax[cur.T];
                 pd = a.tdel[cur.T];
+                if constexpr (FP8) te = a.texp[cur.T];
             }
             if (!mbar_wait(&B->tfull[h], use & 1u, abort, a.st)) break;
             __syncwarp();
@@ -565,6 +600,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             const bool active = us < a.n;
             float hi_t = 0.f, lo_t = 0.f;
             int u_orig = 0;
+            const float f = (FP8 && active) ? pow2i(fp8_exp(um_cur.uexp) + te - 16) : 1.f;  // descale of the FP8 product
             if (active) {
                 const float E = err_bound(a.cacc, a.eabs, um_cur.un, um_cur.unh, um_cur.ud, pnh, pd);
                 hi_t = __fadd_ru(um_cur.tau_hi, E);
@@ -583,6 +619,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                 {
                     float v[32];
                     as_floats(ra, v);
+                    if constexpr (FP8) scale_values(v, f);
                     count_chunk(v, active, c0, pos0 + c0, a.m, hi_t, lo_t, cw, u_orig, a.band, a.band_cap, a.st);
                 }
                 __syncwarp();
@@ -591,6 +628,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                 {
                     float v[32];
                     as_floats(rb, v);
+                    if constexpr (FP8) scale_values(v, f);
                     count_chunk(v, active, c0 + 32, pos0 + c0 + 32, a.m, hi_t, lo_t, cw, u_orig, a.band,
                                 a.band_cap, a.st);
                 }
@@ -644,14 +682,17 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
     return fn;
 }
 
-bool encode_bf16(CUtensorMap* map, const void* base, int64_t rows, int dp, int box_rows) {
+// Tiled map of a packed operand: rows x dp elements of elem_bytes (2 = BF16, 1 = FP8 codes),
+// boxes of box_rows rows x 128 bytes with the 128-byte swizzle.
+bool encode_operand(CUtensorMap* map, const void* base, int64_t rows, int dp, int box_rows, int elem_bytes) {
     auto fn = encode_fn();
     if (!fn) return false;
     cuuint64_t dims[2] = {(cuuint64_t)dp, (cuuint64_t)rows};
-    cuuint64_t strides[1] = {(cuuint64_t)dp * 2u};
-    cuuint32_t box[2] = {64u, (cuuint32_t)box_rows};
+    cuuint64_t strides[1] = {(cuuint64_t)dp * (cuuint64_t)elem_bytes};
+    cuuint32_t box[2] = {(cuuint32_t)(128 / elem_bytes), (cuuint32_t)box_rows};
     cuuint32_t estr[2] = {1u, 1u};
-    CUresult r = fn(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(base), dims, strides, box, estr,
+    const CUtensorMapDataType dt = elem_bytes == 1 ? CU_TENSOR_MAP_DATA_TYPE_UINT8 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16;
+    CUresult r = fn(map, dt, 2, const_cast<void*>(base), dims, strides, box, estr,
                     CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                     CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     return r == CUDA_SUCCESS;
@@ -662,32 +703,45 @@ bool encode_bf16(CUtensorMap* map, const void* base, int64_t rows, int dp, int b
 bool rkm_tc_available() { return true; }
 
 rkm_status make_tmaps(const void* A, int64_t a_rows, const void* B, int64_t b_rows, int dp, int item_tile,
-                      TmapPair* out) {
-    if (dp % 64 != 0 || a_rows % BU != 0 || b_rows % item_tile != 0 || item_tile != BI_TC) return RKM_EINVAL;
+                      int elem_bytes, TmapPair* out) {
+    if (elem_bytes != 1 && elem_bytes != 2) return RKM_EINVAL;
+    if ((dp * elem_bytes) % 128 != 0 || a_rows % BU != 0 || b_rows % item_tile != 0 || item_tile != BI_TC)
+        return RKM_EINVAL;
     if ((reinterpret_cast<uintptr_t>(A) & 15u) || (reinterpret_cast<uintptr_t>(B) & 15u)) return RKM_EINVAL;
-    if (!encode_bf16(&out->a, A, a_rows, dp, BU)) return RKM_ECUDA;
-    if (!encode_bf16(&out->b, B, b_rows, dp, item_tile)) return RKM_ECUDA;
+    if (!encode_operand(&out->a, A, a_rows, dp, BU, elem_bytes)) return RKM_ECUDA;
+    if (!encode_operand(&out->b, B, b_rows, dp, item_tile, elem_bytes)) return RKM_ECUDA;
     return RKM_OK;
 }
 
 void launch_threshold_tc(const TcInstance* inst, int count, long long total_units, int kheap, int max_dp,
-                         int num_sms, cudaStream_t s) {
-    const int KB = max_dp / 64;
+                         bool fp8, int num_sms, cudaStream_t s) {
+    const int KB = fp8 ? max_dp / 128 : max_dp / 64;
     const TcLayout L = make_layout(KB * KB_BYTES_U, KB_BYTES_I, 2u * BU * kheap * 4u + 2u * BU * 8u, MAX_SLOTS);
-    cudaFuncSetAttribute(k_threshold_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.bytes);
     const int grid = (int)(total_units < num_sms ? total_units : num_sms);
     if (grid < 1) return;
     note_launch();
-    k_threshold_tc<<<grid, TC_THREADS, L.bytes, s>>>(inst, count, total_units, kheap, L);
+    if (fp8) {
+        cudaFuncSetAttribute(k_threshold_tc<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.bytes);
+        k_threshold_tc<true><<<grid, TC_THREADS, L.bytes, s>>>(inst, count, total_units, kheap, L);
+    } else {
+        cudaFuncSetAttribute(k_threshold_tc<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.bytes);
+        k_threshold_tc<false><<<grid, TC_THREADS, L.bytes, s>>>(inst, count, total_units, kheap, L);
+    }
 }
 
-void launch_count_tc(const CountArgs& a, const void* tmapA, const void* tmapB, cudaStream_t s) {
-    const int KB = a.dp / 64;
+void launch_count_tc(const CountArgs& a, const void* tmapA, const void* tmapB, bool fp8, cudaStream_t s) {
+    const int KB = fp8 ? a.dp / 128 : a.dp / 64;
     const TcLayout L = make_layout(KB * KB_BYTES_I, KB_BYTES_U, 8u * BI_TC * 4u, MAX_SLOTS);
-    cudaFuncSetAttribute(k_count_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.bytes);
+    const CUtensorMap& mA = *static_cast<const CUtensorMap*>(tmapA);
+    const CUtensorMap& mB = *static_cast<const CUtensorMap*>(tmapB);
     note_launch();
-    k_count_tc<<<a.num_sms, TC_THREADS, L.bytes, s>>>(a, *static_cast<const CUtensorMap*>(tmapA),
-                                                      *static_cast<const CUtensorMap*>(tmapB), L);
+    if (fp8) {
+        cudaFuncSetAttribute(k_count_tc<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.bytes);
+        k_count_tc<true><<<a.num_sms, TC_THREADS, L.bytes, s>>>(a, mA, mB, L);
+    } else {
+        cudaFuncSetAttribute(k_count_tc<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.bytes);
+        k_count_tc<false><<<a.num_sms, TC_THREADS, L.bytes, s>>>(a, mA, mB, L);
+    }
 }
 
 }  // namespace rkm

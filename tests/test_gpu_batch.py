@@ -35,7 +35,7 @@ def expected(W):
     return oracle.topn(oracle.scores_histogram(topk, W.m), W.N)
 
 
-@pytest.mark.parametrize("prec", ["bf16", "fp32"])
+@pytest.mark.parametrize("prec", ["bf16", "fp32", "fp8"])
 def test_batch_matches_oracle_and_replays(rkm, problems, prec):
     ws, probs = problems
     stream = torch.cuda.Stream()

@@ -7,7 +7,8 @@ The oracle cannot score 5e10 (or 1e12) pairs in a test, so:
   GPU (histogram of S_k(u) from rkm_thresholds vs per-item counting from rkm_scores);
 * the filtered top-N of rkm_topn equals the top-N of the full score vector (the Eq. 2
   filter never changes the answer), and the Eq. 2 bound dominates every score (Theorem 2);
-* the BF16 tensor-core path and the FP32 CUDA-core path return identical integers.
+* the BF16 tensor-core path and the FP32 CUDA-core path return identical integers, and so
+  do the FP8 and BF16 tensor-core paths on the 2M x 500K precision workload.
 """
 import numpy as np
 import pytest
@@ -32,7 +33,7 @@ def sample_users(n, count, seed):
     return np.unique(np.r_[0, n - 1, rng.integers(0, n, size=count)])
 
 
-def check_full(rkm, W, prec, sample, check_fp32=False):
+def check_full(rkm, W, prec, sample, check_fp32=False, check_bf16=False):
     U = torch.from_numpy(W.U).cuda()
     P = torch.from_numpy(W.P).cuda()
     with rkm.Context(prec) as ctx:
@@ -59,6 +60,13 @@ def check_full(rkm, W, prec, sample, check_fp32=False):
     ids_o, tops_o = oracle.topn(scores, W.N)
     np.testing.assert_array_equal(ids.cpu().numpy(), ids_o)
     np.testing.assert_array_equal(tops.cpu().numpy(), tops_o)
+    if check_bf16:
+        with rkm.Context("bf16") as c16:
+            i16, s16, t16, d16 = c16.topn(U, P, W.k, W.N, return_thresholds=True)
+        np.testing.assert_array_equal(t16.cpu().numpy().view(np.uint64), tau.view(np.uint64))
+        np.testing.assert_array_equal(d16.cpu().numpy(), tid)
+        np.testing.assert_array_equal(i16.cpu().numpy(), ids_o)
+        np.testing.assert_array_equal(s16.cpu().numpy(), tops_o)
     if check_fp32:
         with rkm.Context("fp32") as c32:
             i32, s32, t32, d32 = c32.topn(U, P, W.k, W.N, return_thresholds=True)
@@ -75,3 +83,11 @@ def test_mf_500k_full_size_bf16_and_fp32_identical(rkm):
 def test_mf_2m_k50_full_size(rkm):
     W = workloads.make("mf-2m-k50")
     check_full(rkm, W, "bf16", sample_users(W.n, 100, 2))
+
+
+def test_mf_2m_k10_full_size_fp8_and_bf16_identical(rkm):
+    """The precision workload (2,000,000 x 500,000, d = 128, k = 10, N = 100): FP8 e4m3
+    products with per-row / per-tile power-of-two scales, checked against the oracle on
+    sampled users and for identity with the BF16 path."""
+    W = workloads.make("mf-2m-k10")
+    check_full(rkm, W, "fp8", sample_users(W.n, 100, 3), check_bf16=True)

@@ -1,5 +1,7 @@
 """Parity of the CUDA path (through the C ABI) with the FP64 oracle.
 
+Every test runs on the three product paths (FP32 CUDA cores, BF16 and FP8 e4m3 tensor
+cores); the guard band and exact rescoring make their integer results identical.
 Integer results (t_u, S_k(u), scores, top-N ids and scores, new-item counts) must be
 identical.  tau_u must be bit-identical on grid inputs (where FP64 is exact); on
 off-grid inputs it must agree with the oracle to 1e-12 relative (the two FP64 sums
@@ -16,7 +18,7 @@ import workloads
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
-PRECISIONS = ["fp32", "bf16"]
+PRECISIONS = ["fp32", "bf16", "fp8"]
 
 
 @pytest.fixture(scope="module")
@@ -213,3 +215,19 @@ def test_adversarial_cancellation_rows(rkm, prec):
     assert oracle.on_grid(U) and oracle.on_grid(P)
     with rkm.Context(prec) as ctx:
         full_check(ctx, U, P, 20, 30)
+
+
+@pytest.mark.parametrize("prec", PRECISIONS)
+def test_extreme_row_magnitudes(rkm, prec):
+    """Rows scaled by 2^70 and 2^-80: the FP8 operand exponent is clamped to [-60, 60], so
+    these rows saturate or underflow in e4m3; the norms of the actual rounding error put
+    their pairs in the guard band, and exact rescoring keeps every result exact."""
+    W = workloads.mf(400, 300, 40, 7, 9, seed=61)
+    U = W.U.copy()
+    U[::5] *= np.float32(2.0 ** 70)
+    U[1::5] *= np.float32(2.0 ** -80)
+    P = W.P.copy()
+    P[::7] *= np.float32(2.0 ** 20)
+    assert oracle.on_grid(U) and oracle.on_grid(P)
+    with rkm.Context(prec) as ctx:
+        full_check(ctx, U, P, W.k, W.N)

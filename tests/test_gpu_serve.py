@@ -46,7 +46,7 @@ def resident():
     return W, tau, tid, arrivals, reqs, expect
 
 
-@pytest.mark.parametrize("prec", ["bf16", "fp32"])
+@pytest.mark.parametrize("prec", ["bf16", "fp32", "fp8"])
 def test_each_request_same_alone_and_in_the_mix(rkm, resident, prec):
     W, tau, tid, arrivals, reqs, expect = resident
     with rkm.Context(prec) as ctx:
