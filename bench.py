@@ -220,6 +220,10 @@ def run_reference(args, rank, world):
     """The FP64 oracle on the host cores: each step is a bounded user sample."""
     if rank != 0:
         return
+    if args.workload == "serve-1m":
+        return run_reference_serve(args)
+    if args.workload == "batch-64":
+        return run_reference_batch(args)
     import oracle
     import workloads
     threads = os.cpu_count() or 1
@@ -246,6 +250,71 @@ def run_reference(args, rank, world):
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
+
+
+def _reference_line(args, value, ms, config, sample, dtype="f64", metric=METRIC):
+    threads = os.cpu_count() or 1
+    return {"impl": "reference", "metric": metric, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": dtype, "data": "synthetic", "config": config,
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
+def run_reference_batch(args):
+    """Oracle on the 64-instance batch: each step scores a user sample of one instance (in turn)
+    against all of its items; value = sampled pairs / time."""
+    import oracle
+    import workloads
+    threads = os.cpu_count() or 1
+    sizes = workloads.batching_instances(64)
+    sample = 16 * threads
+    times, pairs = [], []
+    for step in range(args.warmup + args.steps):
+        sz = sizes[step % len(sizes)]
+        W = workloads.mf(min(sz["n"], sample), sz["m"], sz["d"], sz["k"], sz["N"], seed=sz["seed"])
+        t0 = time.perf_counter()
+        tau, tid, topk = oracle.kmips(W.U, W.P, W.k, block=16, threads=threads)
+        oracle.scores_histogram(topk, W.m)
+        dt = time.perf_counter() - t0
+        if step >= args.warmup:
+            times.append(dt)
+            pairs.append(W.n * W.m)
+    value = sum(pairs) / sum(times)
+    print(json.dumps(_reference_line(
+        args, value, 1000 * statistics.mean(times),
+        {"workload": "batch-64", "instances": len(sizes), "sample_users_per_step": sample},
+        f"users [0,{sample}) of one instance per step x all its items (FP64 thresholds + histogram)")), flush=True)
+
+
+def run_reference_serve(args):
+    """Oracle on the serving workload: thresholds of a user sample against the whole
+    catalogue (not timed), then each step scores one request's candidates against the sample
+    (Definition 2 for new items); value = sampled user-candidate pairs / time."""
+    import oracle
+    import workloads
+    S = workloads.SERVING
+    threads = os.cpu_count() or 1
+    sample = 8 * threads
+    W = workloads.mf(sample, S["m"], S["d"], S["k"], 1, seed=S["catalog_seed"])
+    tau, tid, _ = oracle.kmips(W.U, W.P, W.k, block=8, threads=threads)
+    R = args.warmup + args.steps
+    _, sizes, offsets = workloads.serving_stream(R, 1.0, seed=S["query_seed"])
+    Q = workloads.queries(int(sizes.sum()), W.d, seed=S["query_seed"])
+    times, pairs = [], []
+    for j in range(R):
+        t0 = time.perf_counter()
+        oracle.query_new_items(W.U, tau, Q[offsets[j]:offsets[j] + sizes[j]])
+        dt = time.perf_counter() - t0
+        if j >= args.warmup:
+            times.append(dt)
+            pairs.append(sample * int(sizes[j]))
+    value = sum(pairs) / sum(times)
+    print(json.dumps(_reference_line(
+        args, value, 1000 * statistics.mean(times),
+        {"workload": "serve-1m", "sample_users": sample, "requests": args.steps},
+        f"{sample} resident users (thresholds vs all {S['m']} items) x one request per step",
+        metric="user-item pairs scored/sec (serving what-if queries)")), flush=True)
 
 def workload(args):
     import workloads

@@ -572,31 +572,60 @@ void threshold_exact(rkm_ctx* c, const float* U, int64_t ldu, const float* P, in
                      tau, tid, topk, c->st, s);
 }
 
-// Grow the candidate capacity after an overflow; false when it cannot grow any more.
-rkm_status grow_candidates(rkm_ctx* c, const PathShape& ps, int64_t n, int64_t m, int attempt) {
+// Grow the candidate capacity after an overflow; fails after three retries.
+rkm_status grow_candidates(rkm_ctx* c, int64_t m, int attempt) {
     const int cap = c->cand_cap;
     if (cap >= m || attempt >= 3)
         return fail(RKM_EOVERFLOW, "candidate capacity %d overflowed after %d retries", cap, attempt);
-    const int64_t next = std::min<int64_t>(m, (int64_t)cap * 4);
-    if ((double)n * next * 20.0 * (ps.tc ? 2 : 1) > 64e9)
-        return fail(RKM_EOVERFLOW, "candidate lists need more than 64 GB (n=%lld, cap=%lld)", (long long)n,
-                    (long long)next);
-    c->cand_cap = (int)round_up(next, 32);
+    c->cand_cap = (int)round_up(std::min<int64_t>(m, (int64_t)cap * 4), 32);
     c->stats.retries++;
     return RKM_OK;
 }
 
+// Device bytes the candidate lists of one threshold launch may take (20 bytes per slot:
+// the candidate, its exact key and its id): half of the device memory, at most 48 GB.
+int64_t candidate_budget(const rkm_ctx* c) {
+    size_t free_b = 0, total_b = 0;
+    if (cudaMemGetInfo(&free_b, &total_b) != cudaSuccess) {
+        cudaGetLastError();
+        total_b = (size_t)16 << 30;
+    }
+    return std::min<int64_t>((int64_t)48 << 30, (int64_t)(total_b / 2));
+}
+
+// Rows [u0, u0 + rows) of a prepared side.
+RowPrep row_slice(const RowPrep& r, int64_t u0, int d) {
+    const int64_t dq = round_up(d, 8);
+    return RowPrep{r.e + u0, r.q + u0 * dq, r.n2 + u0, r.nrm + u0, r.nhat + u0, r.del + u0};
+}
+
+// Thresholds of every user, in slices of users small enough that their candidate lists fit
+// the candidate budget (a wide guard band, as on the FP8 path, keeps many candidates per
+// user).  A capacity overflow in any slice grows the capacity and restarts the pass.
 rkm_status thresholds_core(rkm_ctx* c, const PathShape& ps, const float* U, int64_t n, int64_t ldu,
                            const float* P, int64_t ldp, int d, int k, const RowPrep& up, const ItemSide& it,
                            double* tau, int* tid, int* topk, cudaStream_t s) {
     for (int attempt = 0;; ++attempt) {
-        ThrPlan pl;
-        TRY(threshold_prepare(c, ps, U, n, ldu, d, k, up, it, &pl, s));
-        TRY(threshold_launch_one(c, ps, pl, it, s));
-        threshold_exact(c, U, ldu, P, ldp, d, up, it, pl, tau, tid, topk, s);
-        TRY(read_status(c, s));
-        if (!c->st_host->cand_overflow) break;
-        TRY(grow_candidates(c, ps, n, it.m, attempt));
+        const int64_t per_user = (int64_t)(ps.tc ? 2 : 1) * c->cand_cap * 20;
+        const int64_t slice = std::min<int64_t>(n, std::max<int64_t>(BU, candidate_budget(c) / per_user / BU * BU));
+        bool overflow = false;
+        for (int64_t u0 = 0; u0 < n && !overflow; u0 += slice) {
+            const int64_t un = std::min<int64_t>(slice, n - u0);
+            const RowPrep us = row_slice(up, u0, d);
+            ThrPlan pl;
+            TRY(threshold_prepare(c, ps, U + u0 * ldu, un, ldu, d, k, us, it, &pl, s));
+            TRY(threshold_launch_one(c, ps, pl, it, s));
+            threshold_exact(c, U + u0 * ldu, ldu, P, ldp, d, us, it, pl, tau + u0, tid + u0,
+                            topk ? topk + u0 * k : nullptr, s);
+            if (slice < n) TRY(read_status(c, s));  // a single slice is checked below
+            if (slice < n) overflow = c->st_host->cand_overflow != 0;
+        }
+        if (slice >= n) {
+            TRY(read_status(c, s));
+            overflow = c->st_host->cand_overflow != 0;
+        }
+        if (!overflow) break;
+        TRY(grow_candidates(c, it.m, attempt));
         CUDA_TRY(cudaMemsetAsync(&c->st->cand_overflow, 0, sizeof(unsigned), s));
         CUDA_TRY(cudaMemsetAsync(&c->st->internal_error, 0, sizeof(unsigned), s));
         CUDA_TRY(cudaMemsetAsync(&c->st->cand_total, 0, sizeof(unsigned long long), s));
@@ -710,7 +739,9 @@ rkm_status ensure_band(rkm_ctx* c, int2** band) { return c->ensure(c->band, c->b
 // Initial capacities of a call: the option (or a default sized from n and k), or the
 // capacity a previous call on this context grew to, whichever is larger.
 void init_caps(rkm_ctx* c, int64_t n, int k) {
-    int cap = c->opts.cand_capacity > 0 ? c->opts.cand_capacity : (int)round_up(2 * k + 96, 32);
+    // FP8's guard band is about eight times BF16's, so its lists start larger.
+    const int dflt = c->opts.precision == RKM_FP8 ? 8 * k + 256 : 2 * k + 96;
+    int cap = c->opts.cand_capacity > 0 ? c->opts.cand_capacity : (int)round_up(dflt, 32);
     cap = (int)round_up(cap, 32);
     if (c->cand_k == k) cap = std::max(cap, c->cand_cap);
     c->cand_cap = cap;
