@@ -44,6 +44,9 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--n", type=int, default=None, help="override the number of users (profiling cases)")
     ap.add_argument("--m", type=int, default=None, help="override the number of items (profiling cases)")
+    ap.add_argument("--scores", default="count", choices=["count", "histogram"],
+                    help="rkm_topn scores: counting pass with the Eq. 2 filter (default, every step of the"
+                         " path), or the histogram of the exact S_k(u) lists of the threshold pass")
     ap.add_argument("--requests", type=int, default=2000, help="serve-1m: requests per offered load")
     ap.add_argument("--slots", type=int, default=2, help="serve-1m: concurrent batches of the serving loop")
     return ap.parse_args()
@@ -340,7 +343,7 @@ def run_ours(args, rank, local, world):
     U = torch.from_numpy(W.U).cuda()
     P = torch.from_numpy(W.P).cuda()
     flush = torch.empty(512 << 20, dtype=torch.uint8, device="cuda")
-    ctx = rkm.Context(args.precision, device=local, profile=True)
+    ctx = rkm.Context(args.precision, device=local, profile=True, scores_from_topk=args.scores == "histogram")
     for _ in range(args.warmup):
         ctx.topn(U, P, W.k, W.N)
     torch.cuda.synchronize()
@@ -425,6 +428,8 @@ def run_ours(args, rank, local, world):
             "config": {"workload": args.workload if not (args.n or args.m) else f"{args.workload} resized",
                        "n": W.n, "m": W.m, "d": W.d, "k": W.k, "N": W.N,
                        "precision": args.precision, "inputs": "FP32 on the 2^-12 grid, MF-like",
+                       "scores": "counting pass + Eq. 2 filter" if args.scores == "count"
+                                 else "histogram of the exact S_k(u) lists (no counting pass)",
                        "l2": "flushed (512 MiB write) before each timed step",
                        "parallelism": "replicas" if world > 1 else "single GPU"},
             "roofline": roof,

@@ -84,6 +84,10 @@ typedef struct {
     int autotune;            /* rkm_topn_batch: 1 = tune the counting tiles per size
                                 bucket on first sight (default 0)                    */
     const char* tune_cache;  /* file that keeps autotuned choices across runs, or NULL */
+    int scores_from_topk;    /* rkm_topn: 1 = scores as the histogram of the exact S_k(u)
+                                lists of the threshold pass (the first Section 2.2
+                                baseline: n*k increments, no counting pass and no Eq. 2
+                                filter); 0 = counting pass with the filter (default)    */
 } rkm_opts;
 
 /* Phases timed when rkm_opts.profile is set (indices of rkm_stats.phase_ms). */

@@ -37,7 +37,7 @@ class RkmError(RuntimeError):
 class Opts(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int), ("k_max", ctypes.c_int), ("cand_capacity", ctypes.c_int),
                 ("band_capacity", ctypes.c_int64), ("filter", ctypes.c_int), ("profile", ctypes.c_int),
-                ("autotune", ctypes.c_int), ("tune_cache", ctypes.c_char_p)]
+                ("autotune", ctypes.c_int), ("tune_cache", ctypes.c_char_p), ("scores_from_topk", ctypes.c_int)]
 
 
 class Instance(ctypes.Structure):
@@ -154,7 +154,7 @@ def _mat(X):
 
 def rkm_create(precision: str = "bf16", device: int = 0, k_max: int = 64, cand_capacity: int = 0,
                band_capacity: int = 0, filter: bool = True, profile: bool = False, autotune: bool = False,
-               tune_cache: str | None = None) -> ctypes.c_void_p:
+               tune_cache: str | None = None, scores_from_topk: bool = False) -> ctypes.c_void_p:
     lib = load_library()
     o = Opts()
     lib.rkm_default_opts(ctypes.byref(o))
@@ -166,6 +166,7 @@ def rkm_create(precision: str = "bf16", device: int = 0, k_max: int = 64, cand_c
     o.profile = 1 if profile else 0
     o.autotune = 1 if autotune else 0
     o.tune_cache = tune_cache.encode() if tune_cache else None
+    o.scores_from_topk = 1 if scores_from_topk else 0
     h = ctypes.c_void_p()
     _check(lib.rkm_create(ctypes.byref(h), ctypes.byref(o), device))
     return h

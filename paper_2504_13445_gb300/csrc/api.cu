@@ -92,7 +92,7 @@ struct rkm_ctx {
     // bucket sort scratch
     Buf hist, offs;
     // threshold pass
-    Buf cand, cand_cnt, lfin, keys, kid;
+    Buf cand, cand_cnt, lfin, keys, kid, topk_tmp;
     // counting pass
     Buf r_u, uperm, ucum, us_pack, us_meta, nprefix, unit_off, band, cnt_s, top_ids, top_sc, tau_tmp,
         tid_tmp;
@@ -193,7 +193,7 @@ struct rkm_ctx {
     }
 
     void free_all() {
-        Buf* all[] = {&u_e, &u_q, &u_n2, &u_nrm, &u_nhat, &u_del, &u_pack, &p_e, &p_q, &p_n2, &p_nrm,
+        Buf* all[] = {&topk_tmp, &u_e, &u_q, &u_n2, &u_nrm, &u_nhat, &u_del, &u_pack, &p_e, &p_q, &p_n2, &p_nrm,
                       &p_nhat, &p_del, &p_perm, &p_pack, &tmax, &thmax, &tdel, &hist, &offs, &cand,
                       &cand_cnt, &lfin, &keys, &kid, &r_u, &uperm, &ucum, &us_pack, &us_meta,
                       &nprefix, &unit_off, &band, &cnt_s, &top_ids, &top_sc,
@@ -832,6 +832,7 @@ void rkm_default_opts(rkm_opts* o) {
     o->profile = 0;
     o->autotune = 0;
     o->tune_cache = nullptr;
+    o->scores_from_topk = 0;
 }
 
 const char* rkm_last_error(void) { return g_err.c_str(); }
@@ -1085,6 +1086,31 @@ rkm_status rkm_topn(rkm_ctx* c, const float* U, int64_t n, int64_t ldu, const fl
         Phase ph(c, s, RKM_PHASE_PREP);
         TRY(prep_rows(c, ps, U, n, ldu, d, c->u_e, c->u_q, c->u_n2, c->u_nrm, c->u_nhat, c->u_del, &up, s));
         TRY(prep_items(c, ps, P, m, ldp, d, catalogue_bufs(c), &it, s));
+    }
+    if (c->opts.scores_from_topk) {
+        // Scores as the histogram of S_k(u) (the first Section 2.2 baseline): the threshold
+        // pass already ranks every user's candidates exactly, so it writes S_k(u) and the
+        // counting pass is not needed.
+        int *topk, *cnt;
+        TRY(c->ensure(c->topk_tmp, n * (int64_t)k, &topk));
+        TRY(c->ensure(c->cnt_s, m, &cnt));
+        TRY(thresholds_core(c, ps, U, n, ldu, P, ldp, d, k, up, it, tau, tid, topk, s));
+        {
+            Phase ph(c, s, RKM_PHASE_COUNT);
+            CUDA_TRY(cudaMemsetAsync(cnt, 0, m * sizeof(int), s));
+            launch_histogram(topk, n * (int64_t)k, cnt, s);
+        }
+        {
+            Phase ph(c, s, RKM_PHASE_TOPN);
+            launch_topn(cnt, nullptr, m, nullptr, N, ids, top_scores, c->st, s);
+        }
+        TRY(read_status(c, s));
+        if (c->st_host->internal_error) return fail(RKM_EINTERNAL, "top-N: device consistency check failed");
+        c->stats.items_counted = (uint64_t)m;
+        c->stats.pairs_total = (uint64_t)n * (uint64_t)m;
+        c->stats.pairs_evaluated = (uint64_t)n * (uint64_t)m;
+        c->stats.last_ms = now_ms() - t0;
+        return RKM_OK;
     }
     TRY(thresholds_core(c, ps, U, n, ldu, P, ldp, d, k, up, it, tau, tid, nullptr, s));
     const uint64_t cands = c->stats.candidates;

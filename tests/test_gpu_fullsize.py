@@ -7,6 +7,7 @@ The oracle cannot score 5e10 (or 1e12) pairs in a test, so:
   GPU (histogram of S_k(u) from rkm_thresholds vs per-item counting from rkm_scores);
 * the filtered top-N of rkm_topn equals the top-N of the full score vector (the Eq. 2
   filter never changes the answer), and the Eq. 2 bound dominates every score (Theorem 2);
+* rkm_topn with scores as the histogram of S_k(u) (no counting pass) gives the same top N;
 * the BF16 tensor-core path and the FP32 CUDA-core path return identical integers, and so
   do the FP8 and BF16 tensor-core paths on the 2M x 500K precision workload.
 """
@@ -60,6 +61,10 @@ def check_full(rkm, W, prec, sample, check_fp32=False, check_bf16=False):
     ids_o, tops_o = oracle.topn(scores, W.N)
     np.testing.assert_array_equal(ids.cpu().numpy(), ids_o)
     np.testing.assert_array_equal(tops.cpu().numpy(), tops_o)
+    with rkm.Context(prec, scores_from_topk=True) as ch:
+        ih, sh = ch.topn(U, P, W.k, W.N)
+    np.testing.assert_array_equal(ih.cpu().numpy(), ids_o)
+    np.testing.assert_array_equal(sh.cpu().numpy(), tops_o)
     if check_bf16:
         with rkm.Context("bf16") as c16:
             i16, s16, t16, d16 = c16.topn(U, P, W.k, W.N, return_thresholds=True)

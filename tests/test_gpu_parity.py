@@ -231,3 +231,21 @@ def test_extreme_row_magnitudes(rkm, prec):
     assert oracle.on_grid(U) and oracle.on_grid(P)
     with rkm.Context(prec) as ctx:
         full_check(ctx, U, P, W.k, W.N)
+
+
+@pytest.mark.parametrize("prec", PRECISIONS)
+def test_scores_from_topk_option(rkm, prec):
+    """rkm_topn with scores taken as the histogram of the exact S_k(u) lists (no counting
+    pass) gives the same top N as the oracle, with ties at tau_u and at the N-th score."""
+    W = workloads.mf(20_000, 5_000, 64, 25, 50, seed=1)
+    rng = np.random.default_rng(7)
+    Ut = (rng.integers(-64, 65, size=(300, 8)) / 64).astype(np.float32)
+    Pt = np.tile((rng.integers(-64, 65, size=(1, 8)) / 64).astype(np.float32), (90, 1))
+    Pt[40:50] = (rng.integers(-64, 65, size=(10, 8)) / 64).astype(np.float32)
+    for U, P, k, N in ((W.U, W.P, W.k, W.N), (Ut, Pt, 12, 15)):
+        _, _, topk_o = oracle.kmips(U, P, k)
+        ids_o, tops_o = oracle.topn(oracle.scores_histogram(topk_o, P.shape[0]), N)
+        with rkm.Context(prec, scores_from_topk=True) as ctx:
+            ids, tops, tau, tid = ctx.topn(dev(U), dev(P), k, N, return_thresholds=True)
+        np.testing.assert_array_equal(ids.cpu().numpy(), ids_o)
+        np.testing.assert_array_equal(tops.cpu().numpy(), tops_o)
