@@ -170,6 +170,20 @@ RKM_API rkm_status rkm_topn(rkm_ctx* ctx, const float* U, int64_t n, int64_t ldu
                     int32_t* ids, int32_t* top_scores, double* tau, int32_t* tid,
                     void* stream);
 
+/*
+ * Top-N for any k <= kmax from one threshold pass -- the offline/online split of the
+ * paper (Section 4: pre-processing done once, then queries for a given N and k; k_max, the
+ * largest k, is fixed in Section 2.1).  Under the
+ * order above S_k(u) is the first k entries of S_kmax(u), so with lists = the `topk`
+ * output of rkm_thresholds at kmax, score_k(p) = #{u : p among the first k of u's list}
+ * and Definition 3 follows without another product pass.
+ *   lists: device [n * kmax] int32 (row u at u*kmax); 1 <= k <= min(kmax, m);
+ *   1 <= N <= min(m, 4096); ids, top_scores: device [N] int32 as for rkm_topn.
+ *   An id outside [0, m) in the first k entries of a row returns RKM_EINVAL.
+ */
+RKM_API rkm_status rkm_topn_from_topk(rkm_ctx* ctx, const int32_t* lists, int64_t n, int kmax, int k,
+                                      int64_t m, int N, int32_t* ids, int32_t* top_scores, void* stream);
+
 /* rkm_topn with HOST buffers: copies U and P to the device (inside the call),
  * runs rkm_topn and copies ids and top_scores back.  All pointers are host. */
 RKM_API rkm_status rkm_topn_host(rkm_ctx* ctx, const float* U, int64_t n, int64_t ldu,

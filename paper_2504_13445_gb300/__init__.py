@@ -23,7 +23,7 @@ STATUS = {0: "RKM_OK", 1: "RKM_EINVAL", 2: "RKM_ENOMEM", 3: "RKM_ECUDA", 4: "RKM
 EXPORTED = ["rkm_default_opts", "rkm_create", "rkm_destroy", "rkm_last_error", "rkm_version",
             "rkm_thresholds", "rkm_scores", "rkm_topn", "rkm_topn_host", "rkm_item_bounds",
             "rkm_resident_set", "rkm_query_new_items", "rkm_get_stats", "rkm_topn_scores_noalloc",
-            "rkm_topn_batch", "rkm_serve_default_opts", "rkm_serve_create", "rkm_serve_submit",
+            "rkm_topn_batch", "rkm_topn_from_topk", "rkm_serve_default_opts", "rkm_serve_create", "rkm_serve_submit",
             "rkm_serve_wait", "rkm_serve_drain", "rkm_serve_get_stats", "rkm_serve_reset_stats",
             "rkm_serve_destroy"]
 
@@ -109,6 +109,7 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         "rkm_get_stats": (I, [P, ctypes.POINTER(Stats)]),
         "rkm_topn_scores_noalloc": (I, [P, I64, I, P, P, P]),
         "rkm_topn_batch": (I, [P, ctypes.POINTER(Instance), I, P]),
+        "rkm_topn_from_topk": (I, [P, P, I64, I, I, I64, I, P, P, P]),
         "rkm_serve_default_opts": (V, [ctypes.POINTER(ServeOpts)]),
         "rkm_serve_create": (I, [ctypes.POINTER(P), P, ctypes.POINTER(ServeOpts)]),
         "rkm_serve_submit": (I, [P, P, I64, I64, P, ctypes.POINTER(ctypes.c_uint64)]),
@@ -279,6 +280,17 @@ def rkm_topn_batch(ctx, problems, outs=None):
     return new_outs
 
 
+def rkm_topn_from_topk(ctx, lists, m: int, k: int, N: int):
+    """Top N for k <= kmax from the S_kmax(u) lists of rkm_thresholds (device int32 [n, kmax])."""
+    import torch
+    lists = lists.contiguous()
+    n, kmax = lists.shape
+    ids = torch.empty(N, dtype=torch.int32, device=lists.device)
+    sc = torch.empty(N, dtype=torch.int32, device=lists.device)
+    _check(load_library().rkm_topn_from_topk(ctx, _ptr(lists), n, kmax, k, m, N, _ptr(ids), _ptr(sc), _stream()))
+    return ids, sc
+
+
 def rkm_topn_scores_noalloc(scores, N: int):
     """Top N of a device int32 score array through the entry point that allocates no device
     memory (for callers that cannot call cudaMalloc); the output tensors are allocated here,
@@ -389,6 +401,9 @@ class Context:
 
     def topn_batch(self, problems, outs=None):
         return rkm_topn_batch(self.handle, problems, outs)
+
+    def topn_from_topk(self, lists, m, k, N):
+        return rkm_topn_from_topk(self.handle, lists, m, k, N)
 
     def topn_host(self, U, P, k, N):
         return rkm_topn_host(self.handle, U, P, k, N)

@@ -1123,6 +1123,40 @@ rkm_status rkm_topn(rkm_ctx* c, const float* U, int64_t n, int64_t ldu, const fl
     return RKM_OK;
 }
 
+rkm_status rkm_topn_from_topk(rkm_ctx* c, const int32_t* lists, int64_t n, int kmax, int k, int64_t m, int N,
+                              int32_t* ids, int32_t* top_scores, void* stream) {
+    if (!c) return fail(RKM_EINVAL, "null context");
+    if (n < 0 || n > (int64_t)INT32_MAX) return fail(RKM_EINVAL, "n must be in [0, 2^31-1]");
+    if (n > 0 && !lists) return fail(RKM_EINVAL, "null lists");
+    if (m < 1 || m > (int64_t)INT32_MAX) return fail(RKM_EINVAL, "m must be in [1, 2^31-1]");
+    if (kmax < 1 || k < 1 || k > kmax || k > m)
+        return fail(RKM_EINVAL, "k must satisfy 1 <= k <= min(kmax, m) (k=%d, kmax=%d)", k, kmax);
+    if (N < 1 || N > m || N > NMAX_TOPN)
+        return fail(RKM_EINVAL, "N must satisfy 1 <= N <= min(m, %d) (N=%d)", NMAX_TOPN, N);
+    if (!ids || !top_scores) return fail(RKM_EINVAL, "null ids/top_scores");
+    CUDA_TRY(cudaSetDevice(c->device));
+    const double t0 = now_ms();
+    reset_stats(c);
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    TRY(begin_call(c, s));
+    int* cnt;
+    TRY(c->ensure(c->cnt_s, m, &cnt));
+    {
+        Phase ph(c, s, RKM_PHASE_COUNT);
+        CUDA_TRY(cudaMemsetAsync(cnt, 0, m * sizeof(int), s));
+        launch_histogram_prefix(lists, n, kmax, k, m, cnt, c->st, s);
+    }
+    {
+        Phase ph(c, s, RKM_PHASE_TOPN);
+        launch_topn(cnt, nullptr, m, nullptr, N, ids, top_scores, c->st, s);
+    }
+    TRY(read_status(c, s));
+    if (c->st_host->internal_error) return fail(RKM_EINVAL, "lists hold an id outside [0, m) or top-N failed");
+    c->stats.items_counted = (uint64_t)m;
+    c->stats.last_ms = now_ms() - t0;
+    return RKM_OK;
+}
+
 rkm_status rkm_topn_host(rkm_ctx* c, const float* U, int64_t n, int64_t ldu, const float* P, int64_t m,
                          int64_t ldp, int d, int k, int N, int32_t* ids, int32_t* top_scores, void* stream) {
     TRY(check_common(c, d));

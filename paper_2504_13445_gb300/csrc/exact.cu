@@ -167,7 +167,29 @@ __global__ void k_histogram(const int* __restrict__ topk, int64_t nk, int* __res
         atomicAdd(&scores[topk[j]], 1);
 }
 
+// Histogram of the first k ids of every row of lists [n][kmax] (S_k(u) is the first k
+// entries of S_kmax(u) in order).  An id outside [0, m) flags an internal error.
+__global__ void k_histogram_prefix(const int* __restrict__ lists, int64_t n, int kmax, int k, int64_t m,
+                                   int* __restrict__ scores, DevStatus* st) {
+    const int64_t total = n * k;
+    for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < total; j += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t u = j / k;
+        const int id = lists[u * kmax + (j - u * k)];
+        if (id >= 0 && id < m) atomicAdd(&scores[id], 1);
+        else st->internal_error = 1u;
+    }
+}
+
 }  // namespace
+
+void launch_histogram_prefix(const int* lists, int64_t n, int kmax, int k, int64_t m, int* scores, DevStatus* st,
+                             cudaStream_t s) {
+    if (n <= 0 || k <= 0) return;
+    int64_t blocks = (n * k + 255) / 256;
+    if (blocks > 65536) blocks = 65536;
+    note_launch();
+    k_histogram_prefix<<<(int)blocks, 256, 0, s>>>(lists, n, kmax, k, m, scores, st);
+}
 
 void launch_exact_tau(const ExactData& x, const Cand* cand, const int* cand_cnt, const unsigned* lfin_key,
                       int cap, int nseg, const int* item_perm, int64_t n, int k, unsigned long long* keys, int* kid,

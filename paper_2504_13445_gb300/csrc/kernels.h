@@ -146,6 +146,9 @@ void launch_band_rescore(const ExactData& x, const int2* band, unsigned band_cap
 
 // K8: scores by histogram of S_k(u) (the first Section 2.2 baseline).
 void launch_histogram(const int* topk, int64_t nk, int* scores, cudaStream_t s);
+// Same over the first k entries of each row of lists [n][kmax] (ids checked against [0, m)).
+void launch_histogram_prefix(const int* lists, int64_t n, int kmax, int k, int64_t m, int* scores, DevStatus* st,
+                             cudaStream_t s);
 
 // ---- counting pass (K5) -------------------------------------------------------------
 

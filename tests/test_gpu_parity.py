@@ -249,3 +249,21 @@ def test_scores_from_topk_option(rkm, prec):
             ids, tops, tau, tid = ctx.topn(dev(U), dev(P), k, N, return_thresholds=True)
         np.testing.assert_array_equal(ids.cpu().numpy(), ids_o)
         np.testing.assert_array_equal(tops.cpu().numpy(), tops_o)
+
+
+@pytest.mark.parametrize("prec", PRECISIONS)
+def test_topn_for_every_k_from_one_pass(rkm, prec):
+    """One threshold pass at k_max = 50 keeps S_kmax(u); the top N for k = 1, 7, 25, 50 then
+    follow from its prefixes (Section 4's offline/online split) and equal the oracle's."""
+    W = workloads.mf(8_000, 3_000, 48, 50, 40, seed=17)
+    kmax = 50
+    with rkm.Context(prec) as ctx:
+        _, _, lists = ctx.thresholds(dev(W.U), dev(W.P), kmax, want_topk=True)
+        for k in (1, 7, 25, 50):
+            _, _, topk_o = oracle.kmips(W.U, W.P, k)
+            ids_o, tops_o = oracle.topn(oracle.scores_histogram(topk_o, W.m), W.N)
+            ids, tops = ctx.topn_from_topk(lists, W.m, k, W.N)
+            np.testing.assert_array_equal(ids.cpu().numpy(), ids_o)
+            np.testing.assert_array_equal(tops.cpu().numpy(), tops_o)
+        with pytest.raises(rkm.RkmError):
+            ctx.topn_from_topk(lists, W.m, kmax + 1, W.N)
