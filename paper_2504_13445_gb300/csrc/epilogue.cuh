@@ -58,6 +58,8 @@ struct SelState {
     int cnt;     // candidates stored
     unsigned long long* pub;  // where this group publishes its bound for the other (null: none)
     unsigned tag;             // user tile the published bound belongs to
+    int defer;   // 1: hits only record candidates; sel_merge_tile admits them at the tile's end
+    int mark;    // first candidate recorded in the current tile (-1 after a compaction in it)
 };
 
 // The best lower bound of tau_u this group knows.
@@ -106,7 +108,10 @@ __device__ __forceinline__ void sel_insert(float v, int pos, float E, SelState& 
                                            float* heap, int t, int k, DevStatus* st) {
     const float ub = __fadd_ru(v, E);
     const float lb = __fsub_rd(v, E);
-    if (s.cnt >= cap) s.cnt = compact_candidates(mycand, s.cnt, sel_bound(s));
+    if (s.cnt >= cap) {
+        s.cnt = compact_candidates(mycand, s.cnt, sel_bound(s));
+        s.mark = -1;
+    }
     if (s.cnt < cap) {
         Cand c;
         c.ub = ub;
@@ -115,6 +120,7 @@ __device__ __forceinline__ void sel_insert(float v, int pos, float E, SelState& 
     } else {
         st->cand_overflow = 1u;
     }
+    if (s.defer) return;
     if (lb > sel_bound(s)) {
         if (s.hn < k) {
             heap[s.hn * BU + t] = lb;
@@ -127,6 +133,48 @@ __device__ __forceinline__ void sel_insert(float v, int pos, float E, SelState& 
         if (s.pub) publish_bound(s.pub, s.tag, fmaxf(s.L, s.Lw));
         s.thr = __fsub_rd(sel_bound(s), E);
     }
+}
+
+// A lower bound of u.p for a candidate recorded with ub = RU(v + E) in a tile whose products
+// have error bound E: v >= ub - E - ulp(ub), so u.p >= v - E >= ub - 2E - ulp(ub) (the ulp
+// taken as |ub| 2^-23 + 2^-149, every step rounded down).
+__device__ __forceinline__ float cand_lower(float ub, float E) {
+    const float d = __fadd_ru(__fmul_ru(fabsf(ub), 0x1p-23f), 0x1p-149f);
+    return __fsub_rd(__fsub_rd(__fsub_rd(ub, E), E), d);
+}
+
+// Deferred admissions: the lower bounds of the candidates recorded since the tile started
+// enter the heap at the tile's end, with every lane of the warp stepping through its own
+// list together (the heap is built at most once per lane, in one place, instead of at the
+// hit that completes it).  Skipping admissions is sound (see sel_insert), so a tile whose
+// entries a compaction moved admits nothing.
+__device__ __forceinline__ void sel_merge_tile(SelState& s, const Cand* mycand, float* heap, int t, int k, float E,
+                                               bool active) {
+    const int j0 = s.mark, j1 = s.cnt;
+    s.mark = s.cnt;
+    if (!active || j0 < 0 || j0 >= j1) return;
+    const float L0 = sel_bound(s);
+    int j = j0;
+    bool filled = false;
+    for (; j < j1 && s.hn < k; ++j) {
+        const float lb = cand_lower(mycand[j].ub, E);
+        if (lb > L0) {
+            heap[s.hn * BU + t] = lb;
+            if (++s.hn == k) filled = true;
+        }
+    }
+    if (filled) {
+        heapify(heap, t, k);
+        s.L = heap[t];
+    }
+    for (; j < j1; ++j) {
+        const float lb = cand_lower(mycand[j].ub, E);
+        if (lb > sel_bound(s)) {
+            heap_replace_root(heap, t, k, lb);
+            s.L = heap[t];
+        }
+    }
+    if (s.hn == k && s.pub) publish_bound(s.pub, s.tag, fmaxf(s.L, s.Lw));
 }
 
 // x = v[c] for a run-time c in [0, 32): a five-level select tree (no local memory).

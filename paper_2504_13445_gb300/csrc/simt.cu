@@ -115,6 +115,8 @@ __global__ void __launch_bounds__(SIMT_THREADS, 1) k_threshold_simt(ThresholdArg
         s.cnt = 0;
         s.pub = nullptr;
         s.tag = 0u;
+        s.defer = 0;
+        s.mark = 0;
         float un = 0.f, unh = 0.f, ud = 0.f;
         Cand* mycand = nullptr;
         if (owner) {

@@ -290,6 +290,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             s.cnt = 0;
             s.pub = &Lpub[h * BU + r];
             s.tag = (unsigned)w;
+            s.defer = 1;
+            s.mark = 0;
             bool warm = false;  // warm start done for this unit
             const float un = active ? a.unrm[u] : 0.f;
             const float unh = active ? a.unhat[u] : 0.f;
@@ -371,6 +373,9 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                 tc_fence_before();
                 __syncwarp();
                 if (lane == 0) mbar_arrive(&B->tempty[b]);
+                // The accumulator is released: admit this tile's candidates while the MMA
+                // computes the next tiles.
+                sel_merge_tile(s, mycand, heap, r, a.k, E, active);
             }
             if (active) {
                 atomicMax(&a.lfin_key[u], float_key(fmaxf(s.L, s.Lw)));
