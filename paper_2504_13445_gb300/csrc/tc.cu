@@ -331,14 +331,15 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                     // First tile of this group for these users: a lockstep first pass over the
                     // accumulator gives a lower bound before any candidate is recorded, so the
                     // heap does not fill one divergent insertion at a time: the k-th largest of
-                    // 32 maxima of 8 columns (k <= 32) or of 64 maxima of 4 columns (k <= 64).
+                    // 64 maxima of 4 columns (k <= 64 distinct items reach it).  Hits of this
+                    // tile are recorded against it until the tile's end, so its tightness sets
+                    // how many candidates the first tile records.
                     auto load = [&](int c0, float (&v)[32]) {
                         __syncwarp();
                         tmem_ld32(tb + c0, v);
                         if constexpr (FP8) scale_values(v, f);
                     };
-                    const float lw = a.k <= 32 ? warm_bound<32, BI_TC>(load, it * BI_TC, a.m, a.k, E)
-                                               : warm_bound<64, BI_TC>(load, it * BI_TC, a.m, a.k, E);
+                    const float lw = warm_bound<64, BI_TC>(load, it * BI_TC, a.m, a.k, E);
                     s.Lw = active ? lw : -INFINITY;
                     publish_bound(s.pub, s.tag, s.Lw);
                     warm = true;
