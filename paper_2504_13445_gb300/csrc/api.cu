@@ -447,7 +447,7 @@ rkm_status prep_items(rkm_ctx* c, const PathShape& ps, const float* P, int64_t m
     it->tiles = (m + ps.item_tile - 1) / ps.item_tile;
     TRY(prep_rows(c, ps, P, m, ldp, d, bb.e, bb.q, bb.n2, bb.nrm, bb.nhat, bb.del, &it->rp, s, true));
     unsigned *hist, *offs;
-    TRY(c->ensure(c->hist, NBUCKET, &hist));
+    TRY(c->ensure(c->hist, HIST_WORDS, &hist));
     TRY(c->ensure(c->offs, NBUCKET, &offs));
     TRY(c->ensure(bb.perm, m, &it->perm));
     launch_bucket_sort(it->rp.nrm, m, true, hist, offs, it->perm, nullptr, s);
@@ -654,7 +654,7 @@ rkm_status order_users(rkm_ctx* c, const PathShape& ps, const float* U, int64_t 
     float* r;
     unsigned *hist, *offs;
     TRY(c->ensure(c->r_u, n, &r));
-    TRY(c->ensure(c->hist, NBUCKET, &hist));
+    TRY(c->ensure(c->hist, HIST_WORDS, &hist));
     TRY(c->ensure(c->offs, NBUCKET, &offs));
     TRY(c->ensure(bb.perm, n, &uo->uperm));
     TRY(c->ensure(bb.cum, NBUCKET, &uo->ucum));
@@ -1199,7 +1199,7 @@ rkm_status rkm_item_bounds(rkm_ctx* c, const float* U, int64_t n, int64_t ldu, c
     unsigned *hist, *offs, *ucum;
     int* uperm;
     TRY(c->ensure(c->r_u, std::max<int64_t>(n, 1), &r));
-    TRY(c->ensure(c->hist, NBUCKET, &hist));
+    TRY(c->ensure(c->hist, HIST_WORDS, &hist));
     TRY(c->ensure(c->offs, NBUCKET, &offs));
     TRY(c->ensure(c->uperm, std::max<int64_t>(n, 1), &uperm));
     TRY(c->ensure(c->ucum, NBUCKET, &ucum));

@@ -15,6 +15,9 @@ constexpr int BI_TC = 256;
 constexpr int KMAX = 64;          // largest k the on-chip heaps hold
 constexpr int NMAX_TOPN = 4096;   // largest N the single-CTA top-N select holds
 constexpr int NBUCKET = 65536;    // buckets of the 16-bit float keys
+constexpr int SCAN_BLOCK = 1024;  // buckets per block of the bucket-count prefix scan
+constexpr int SCAN_BLOCKS = NBUCKET / SCAN_BLOCK;
+constexpr int HIST_WORDS = NBUCKET + SCAN_BLOCKS;  // bucket counts, then per-block totals
 
 // Device-side status and counters of one call.  Zeroed before each call.
 struct DevStatus {

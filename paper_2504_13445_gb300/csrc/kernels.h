@@ -55,7 +55,7 @@ void launch_pack_bf16(const float* X, int64_t rows, int64_t ld, int d, const int
 
 // Counting sort of `count` float keys by their 16-bit bucket (ascending, or descending
 // when `descending`).  Writes perm[pos] = source index and, if cum != null, the
-// inclusive prefix count of each bucket (in sort order).  hist: NBUCKET uints scratch.
+// inclusive prefix count of each bucket (in sort order).  hist: HIST_WORDS uints scratch.
 void launch_bucket_sort(const float* keys, int64_t count, bool descending, unsigned* hist,
                         unsigned* offs, int* perm, unsigned* cum, cudaStream_t s);
 

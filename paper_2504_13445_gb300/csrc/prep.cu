@@ -191,31 +191,55 @@ __global__ void k_hist(const float* __restrict__ keys, int64_t count, bool desc,
     }
 }
 
-// Single block: exclusive scan of hist into offs, inclusive into cum (if non-null).
-__global__ void k_scan_hist(const unsigned* __restrict__ hist, unsigned* __restrict__ offs,
-                            unsigned* __restrict__ cum) {
-    constexpr int T = 1024;
-    constexpr int PER = NBUCKET / T;  // 64 consecutive buckets per thread
-    __shared__ unsigned part[T];
-    const int t = threadIdx.x;
-    unsigned local = 0;
-    for (int j = 0; j < PER; ++j) local += hist[t * PER + j];
-    part[t] = local;
+// Exclusive scan of the bucket counts hist into offs and inclusive into cum (if non-null), in
+// two launches of SCAN_BLOCKS blocks with coalesced accesses: each block scans its SCAN_BLOCK
+// buckets (warp shuffles, then the warp totals) and records its total; then each block adds
+// the totals of the blocks before it.
+__global__ void __launch_bounds__(SCAN_BLOCK) k_scan_part(const unsigned* __restrict__ hist,
+                                                          unsigned* __restrict__ offs,
+                                                          unsigned* __restrict__ totals) {
+    __shared__ unsigned wsum[SCAN_BLOCK / 32];
+    const int t = threadIdx.x, lane = t & 31, w = t >> 5;
+    const int i = blockIdx.x * SCAN_BLOCK + t;
+    const unsigned h = hist[i];
+    unsigned x = h;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const unsigned y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) wsum[w] = x;
     __syncthreads();
-    // Hillis-Steele inclusive scan over the 1024 partial sums.
-    for (int o = 1; o < T; o <<= 1) {
-        unsigned v = (t >= o) ? part[t - o] : 0u;
-        __syncthreads();
-        part[t] += v;
-        __syncthreads();
+    if (w == 0) {
+        unsigned z = wsum[lane];
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const unsigned y = __shfl_up_sync(0xffffffffu, z, o);
+            if (lane >= o) z += y;
+        }
+        wsum[lane] = z;
     }
-    unsigned run = part[t] - local;
-    for (int j = 0; j < PER; ++j) {
-        unsigned h = hist[t * PER + j];
-        offs[t * PER + j] = run;
-        run += h;
-        if (cum) cum[t * PER + j] = run;
+    __syncthreads();
+    offs[i] = (w > 0 ? wsum[w - 1] : 0u) + x - h;
+    if (t == SCAN_BLOCK - 1) totals[blockIdx.x] = wsum[SCAN_BLOCK / 32 - 1];
+}
+
+__global__ void __launch_bounds__(SCAN_BLOCK) k_scan_fix(const unsigned* __restrict__ hist,
+                                                         unsigned* __restrict__ offs, unsigned* __restrict__ cum,
+                                                         const unsigned* __restrict__ totals) {
+    __shared__ unsigned base;
+    const int t = threadIdx.x;
+    if (t < 32) {
+        unsigned z = 0u;
+        for (int j = t; j < (int)blockIdx.x; j += 32) z += totals[j];
+        z = warp_sum(z);
+        if (t == 0) base = z;
     }
+    __syncthreads();
+    const int i = blockIdx.x * SCAN_BLOCK + t;
+    const unsigned o = offs[i] + base;
+    offs[i] = o;
+    if (cum) cum[i] = o + hist[i];
 }
 
 __global__ void k_scatter(const float* __restrict__ keys, int64_t count, bool desc,
@@ -360,7 +384,9 @@ void launch_bucket_sort(const float* keys, int64_t count, bool descending, unsig
         k_hist<<<grid_for(count, 256, 4096), 256, 0, s>>>(keys, count, descending, hist);
     }
     note_launch();
-    k_scan_hist<<<1, 1024, 0, s>>>(hist, offs, cum);
+    k_scan_part<<<SCAN_BLOCKS, SCAN_BLOCK, 0, s>>>(hist, offs, hist + NBUCKET);
+    note_launch();
+    k_scan_fix<<<SCAN_BLOCKS, SCAN_BLOCK, 0, s>>>(hist, offs, cum, hist + NBUCKET);
     if (count > 0) {
         note_launch();
         k_scatter<<<grid_for(count, 256, 4096), 256, 0, s>>>(keys, count, descending, offs, perm);
