@@ -32,56 +32,63 @@ inline int grid_for(int64_t work, int per_block, int cap = 1 << 20) {
     return (int)g;
 }
 
-// One warp per row.  The row is on the grid iff every x * 2^(12-e) is an integer of
-// magnitude <= 4096; then ||x||^2 = sum(q^2) * 2^(2e-24) exactly.
+// A segment of lpr lanes per row (lpr a power of two, 32 / lpr rows per warp, so that short
+// rows do not leave most of a warp's reductions idle).  The row is on the grid iff every
+// x * 2^(12-e) is an integer of magnitude <= 4096; then ||x||^2 = sum(q^2) * 2^(2e-24) exactly.
 __global__ void k_prep_rows(const float* __restrict__ X, int64_t rows, int64_t ld, int d,
                             int* __restrict__ ex, int16_t* __restrict__ q, int dq,
                             double* __restrict__ norm2, float* __restrict__ nrm_hi,
                             float* __restrict__ nhat_hi, float* __restrict__ del_hi, int operand,
-                            unsigned* grid_flag) {
+                            unsigned* grid_flag, int lpr) {
     const int lane = threadIdx.x & 31;
+    const int sub = lane & (lpr - 1);
+    const int rpw = 32 / lpr;
     const int64_t warps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    for (int64_t row = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; row < rows; row += warps) {
-        const float* x = X + row * ld;
+    for (int64_t r0 = (((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5) * rpw; r0 < rows; r0 += warps * rpw) {
+        const int64_t row = r0 + lane / lpr;
+        const bool valid = row < rows;
+        const float* x = X + (valid ? row : 0) * ld;
         float mx = 0.f;
-        for (int j = lane; j < d; j += 32) mx = fmaxf(mx, fabsf(x[j]));
-        mx = warp_max(mx);
+        if (valid)
+            for (int j = sub; j < d; j += lpr) mx = fmaxf(mx, fabsf(x[j]));
+        for (int o = lpr >> 1; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
         int e = 0;
         if (mx > 0.f) {
             int E;
             float f = frexpf(mx, &E);
             e = (f == 0.5f) ? E - 1 : E;
         }
-        bool ok = true;
+        int ok = 1;
         long long s2 = 0;
         // Upper bounds of sums of squares: every FP32 operation rounds up.
         float d2 = 0.f, h2 = 0.f, e2 = 0.f;
-        for (int j = lane; j < dq; j += 32) {
-            float v = (j < d) ? x[j] : 0.f;
-            float t = ldexpf(v, 12 - e);
-            bool gi = (t == rintf(t)) && fabsf(t) <= 4096.f;
-            ok = ok && gi;
-            int qi = gi ? (int)t : 0;
-            q[row * dq + j] = (int16_t)qi;
-            s2 += (long long)qi * qi;
-            d2 = __fmaf_ru(v, v, d2);
-            // Operand the product kernels see, and its rounding error (exact in FP32).
-            float vh = v;
-            if (operand == OPERAND_BF16) vh = __bfloat162float(__float2bfloat16_rn(v));
-            if (operand == OPERAND_FP8_ROW) vh = ldexpf(fp8_scaled(v, fp8_exp(e), nullptr), fp8_exp(e) - 8);
-            const float dv = vh - v;
-            h2 = __fmaf_ru(vh, vh, h2);
-            e2 = __fmaf_ru(dv, dv, e2);
+        if (valid) {
+            for (int j = sub; j < dq; j += lpr) {
+                float v = (j < d) ? x[j] : 0.f;
+                float t = ldexpf(v, 12 - e);
+                bool gi = (t == rintf(t)) && fabsf(t) <= 4096.f;
+                ok = ok & (gi ? 1 : 0);
+                int qi = gi ? (int)t : 0;
+                q[row * dq + j] = (int16_t)qi;
+                s2 += (long long)qi * qi;
+                d2 = __fmaf_ru(v, v, d2);
+                // Operand the product kernels see, and its rounding error (exact in FP32).
+                float vh = v;
+                if (operand == OPERAND_BF16) vh = __bfloat162float(__float2bfloat16_rn(v));
+                if (operand == OPERAND_FP8_ROW) vh = ldexpf(fp8_scaled(v, fp8_exp(e), nullptr), fp8_exp(e) - 8);
+                const float dv = vh - v;
+                h2 = __fmaf_ru(vh, vh, h2);
+                e2 = __fmaf_ru(dv, dv, e2);
+            }
         }
-        ok = __all_sync(0xffffffffu, ok);
-        s2 = warp_sum(s2);
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
+        for (int o = lpr >> 1; o > 0; o >>= 1) {
+            ok &= __shfl_xor_sync(0xffffffffu, ok, o);
+            s2 += __shfl_xor_sync(0xffffffffu, s2, o);
             d2 = __fadd_ru(d2, __shfl_xor_sync(0xffffffffu, d2, o));
             h2 = __fadd_ru(h2, __shfl_xor_sync(0xffffffffu, h2, o));
             e2 = __fadd_ru(e2, __shfl_xor_sync(0xffffffffu, e2, o));
         }
-        if (lane == 0) {
+        if (valid && sub == 0) {
             double n2;
             if (ok) {
                 n2 = ldexp((double)s2, 2 * e - 24);  // exact
@@ -338,10 +345,14 @@ void launch_prep_rows(const float* X, int64_t rows, int64_t ld, int d, int* ex, 
                       double* norm2, float* nrm_hi, float* nhat_hi, float* del_hi, int operand,
                       DevStatus* st, cudaStream_t s) {
     if (rows <= 0) return;
+    // Lanes per row: about 8 elements per lane, between 4 and 32 lanes.
+    int lpr = 4;
+    while (lpr < 32 && lpr * 8 < dq) lpr <<= 1;
+    const int64_t warps = (rows + (32 / lpr) - 1) / (32 / lpr);
     note_launch();
-    k_prep_rows<<<grid_for(rows * 32, 256, 65536), 256, 0, s>>>(X, rows, ld, d, ex, q, dq, norm2,
-                                                                 nrm_hi, nhat_hi, del_hi, operand,
-                                                                 &st->off_grid);
+    k_prep_rows<<<grid_for(warps * 32, 256, 65536), 256, 0, s>>>(X, rows, ld, d, ex, q, dq, norm2,
+                                                                  nrm_hi, nhat_hi, del_hi, operand,
+                                                                  &st->off_grid, lpr);
 }
 
 void launch_pack_fp8(const float* X, int64_t rows, int64_t ld, int d, const int* perm, const int* row_exp,
