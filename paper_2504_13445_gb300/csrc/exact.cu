@@ -61,7 +61,9 @@ __device__ __forceinline__ float key_to_float(unsigned k) {
     return __uint_as_float(b);
 }
 
-__global__ void k_exact_tau(ExactData x, const Cand* __restrict__ cand, const int* __restrict__ cand_cnt,
+// Latency-bound (dependent loads of each user's candidates, ids and codes): six blocks per
+// SM (40 registers, a few spilled) hide more of it than the four that 63 registers allow.
+__global__ void __launch_bounds__(256, 6) k_exact_tau(ExactData x, const Cand* __restrict__ cand, const int* __restrict__ cand_cnt,
                             const unsigned* __restrict__ lfin_key, int cap, int nseg,
                             const int* __restrict__ item_perm,
                             int64_t n, int k, unsigned long long* __restrict__ keys,
