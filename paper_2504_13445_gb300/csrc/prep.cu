@@ -114,20 +114,28 @@ __device__ __forceinline__ __nv_bfloat16 cvt_from_float<__nv_bfloat16>(float v) 
     return __float2bfloat16_rn(v);
 }
 
+// Eight consecutive columns per thread (dp is a multiple of 8), written as one 16-byte
+// (BF16) or two 16-byte (FP32) stores.
 template <typename T>
 __global__ void k_pack(const float* __restrict__ X, int64_t rows, int64_t ld, int d,
                        const int* __restrict__ perm, T* __restrict__ dst, int64_t rows_pad, int dp) {
-    const int64_t total = rows_pad * dp;
+    const int cpr = dp >> 3;  // 8-column chunks per row
+    const int64_t total = rows_pad * cpr;
     for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
          idx += (int64_t)gridDim.x * blockDim.x) {
-        int64_t r = idx / dp;
-        int c = (int)(idx - r * dp);
-        float v = 0.f;
-        if (r < rows && c < d) {
-            int64_t src = perm ? (int64_t)perm[r] : r;
-            v = X[src * ld + c];
-        }
-        dst[idx] = cvt_from_float<T>(v);
+        const int64_t r = idx / cpr;
+        const int c0 = (int)(idx - r * cpr) * 8;
+        float v[8];
+        const float* x = (r < rows) ? X + (perm ? (int64_t)perm[r] : r) * ld : nullptr;
+#pragma unroll
+        for (int j = 0; j < 8; ++j) v[j] = (x && c0 + j < d) ? x[c0 + j] : 0.f;
+        T out[8];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) out[j] = cvt_from_float<T>(v[j]);
+        uint4* o = reinterpret_cast<uint4*>(dst + r * dp + c0);
+        const uint4* src = reinterpret_cast<const uint4*>(out);
+#pragma unroll
+        for (int w = 0; w < (int)(8 * sizeof(T) / 16); ++w) o[w] = src[w];
     }
 }
 
@@ -375,16 +383,16 @@ void launch_pack_f32(const float* X, int64_t rows, int64_t ld, int d, const int*
                      int64_t rows_pad, int dp, cudaStream_t s) {
     if (rows_pad <= 0) return;
     note_launch();
-    k_pack<float><<<grid_for(rows_pad * dp, 256, 65536), 256, 0, s>>>(X, rows, ld, d, perm, dst,
-                                                                      rows_pad, dp);
+    k_pack<float><<<grid_for(rows_pad * (dp / 8), 256, 65536), 256, 0, s>>>(X, rows, ld, d, perm, dst,
+                                                                            rows_pad, dp);
 }
 
 void launch_pack_bf16(const float* X, int64_t rows, int64_t ld, int d, const int* perm,
                       __nv_bfloat16* dst, int64_t rows_pad, int dp, cudaStream_t s) {
     if (rows_pad <= 0) return;
     note_launch();
-    k_pack<__nv_bfloat16><<<grid_for(rows_pad * dp, 256, 65536), 256, 0, s>>>(X, rows, ld, d, perm,
-                                                                              dst, rows_pad, dp);
+    k_pack<__nv_bfloat16><<<grid_for(rows_pad * (dp / 8), 256, 65536), 256, 0, s>>>(X, rows, ld, d, perm,
+                                                                                    dst, rows_pad, dp);
 }
 
 void launch_bucket_sort(const float* keys, int64_t count, bool descending, unsigned* hist,
