@@ -1,9 +1,12 @@
 #!/usr/bin/env python
 """Benchmark of the reverse k-MIPS top-N hot path on one GB300 (or N replicas).
 
-One step = one rkm_topn call on the MF-like workload users n=500,000, items m=100,000,
-d=64, k=25, N=50 (FP32 grid inputs, resident in HBM): prep, thresholds (product +
-selector + exact rescoring), Eq. 2 bounds, filtered counting, band rescoring, top-N.
+One step = one rkm_topn call on the largest single-GPU workload, MF-like users
+n=2,000,000, items m=500,000, d=128, k=10, N=100 (FP32 grid inputs, resident in HBM):
+prep, thresholds (product + selector + exact rescoring), Eq. 2 bounds, filtered counting,
+band rescoring, top-N.  After the timed BF16 steps the same inputs run once through the
+FP8 and the plain exact FP32 paths; their top-N, tau_u and t_u must equal the BF16 path's
+bit for bit (the run fails otherwise) and the step-time ratios are reported.
 
 metric: user-item pairs scored per second = n*m / step time (the dense pair count of
 the problem, whatever the filter skips).  L2 is flushed (a 512 MiB write) before each
@@ -38,7 +41,7 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--precision", default="bf16", choices=["bf16", "fp8", "fp32"])
-    ap.add_argument("--workload", default="mf-500k")
+    ap.add_argument("--workload", default="mf-2m-k10")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
@@ -47,6 +50,8 @@ def parse():
     ap.add_argument("--scores", default="count", choices=["count", "histogram"],
                     help="rkm_topn scores: counting pass with the Eq. 2 filter (default, every step of the"
                          " path), or the histogram of the exact S_k(u) lists of the threshold pass")
+    ap.add_argument("--no-compare", action="store_true",
+                    help="skip the FP8 and FP32 runs on the same inputs (identical results, speedups)")
     ap.add_argument("--requests", type=int, default=2000, help="serve-1m: requests per offered load")
     ap.add_argument("--slots", type=int, default=2, help="serve-1m: concurrent batches of the serving loop")
     return ap.parse_args()
@@ -162,13 +167,16 @@ def threshold_traffic(workload: str):
     return THRESHOLD_TRAFFIC.get(h.hexdigest(), {}).get(workload)
 
 
-def tensor_peak(peaks: dict, precision: str):
-    """Dense tensor peak of the product's dtype: the measured BF16 burst figure, times the
+def tensor_peak(peaks: dict, precision: str, sustained: bool = False):
+    """Dense tensor peak of the product's dtype: the measured BF16 figure (burst for a kernel
+    timed alone, sustained for one timed inside a seconds-long run of steps), times the
     nominal FP8/BF16 ratio (4.5 / 2.25 PFLOP/s) for FP8."""
-    bf16 = peaks["bf16_tflops"]
+    key = "bf16_tflops_sustained" if sustained and "bf16_tflops_sustained" in peaks else "bf16_tflops"
+    kind = "sustained" if key.endswith("sustained") else "burst"
+    bf16 = peaks[key]
     if precision == "fp8":
-        return 2.0 * bf16, f"{peaks['source']} bf16_tflops (burst) x 2 (nominal FP8/BF16 dense ratio)"
-    return bf16, f"{peaks['source']} bf16_tflops (burst)"
+        return 2.0 * bf16, f"{peaks['source']} {key} ({kind}) x 2 (nominal FP8/BF16 dense ratio)"
+    return bf16, f"{peaks['source']} {key} ({kind})"
 
 
 DTYPE = {"bf16": "bf16", "fp8": "e4m3", "fp32": "f32"}
@@ -203,20 +211,21 @@ def _cpu_child(cfg, k, seconds, q, n=None, m=None):
     import oracle
     import workloads
     over = {key: v for key, v in (("n", n), ("m", m)) if v}
-    W = workloads.make(cfg, **over)
+    n_all = dict(workloads.CONFIGS[cfg], **over)["n"]
+    P = workloads.rows(cfg, "P", **over)
     block = 64 * threads
-    t0 = time.perf_counter()
-    done = 0
+    done, dt = 0, 0.0
     while True:
-        u1 = min(W.n, done + block)
-        tau, tid, topk = oracle.kmips(W.U[done:u1], W.P, k, block=64, threads=threads)
-        oracle.scores_histogram(topk, W.m)
-        done = u1
-        if time.perf_counter() - t0 >= seconds or done >= W.n:
+        Ub = workloads.rows(cfg, "U", done, block, **over)  # drawn outside the timed work
+        t0 = time.perf_counter()
+        tau, tid, topk = oracle.kmips(Ub, P, k, block=64, threads=threads)
+        oracle.scores_histogram(topk, P.shape[0])
+        dt += time.perf_counter() - t0
+        done += Ub.shape[0]
+        if dt >= seconds or done >= n_all:
             break
-    dt = time.perf_counter() - t0
-    q.put({"value": done * W.m / dt, "unit": UNIT, "cores": threads, "kind": "oracle",
-           "sample": f"users [0,{done}) x all {W.m} items of {cfg}: FP64 thresholds + histogram, {dt:.1f} s"})
+    q.put({"value": done * P.shape[0] / dt, "unit": UNIT, "cores": threads, "kind": "oracle",
+           "sample": f"users [0,{done}) x all {P.shape[0]} items of {cfg}: FP64 thresholds + histogram, {dt:.1f} s"})
 
 
 def run_reference(args, rank, world):
@@ -230,26 +239,32 @@ def run_reference(args, rank, world):
     import oracle
     import workloads
     threads = os.cpu_count() or 1
-    W = workload(args)
-    sample = 32 * threads
+    over = {key: v for key, v in (("n", args.n), ("m", args.m)) if v}
+    cfg = dict(workloads.CONFIGS[args.workload], **over)
+    P = workloads.rows(args.workload, "P", **over)
+    # The same blocking as the cpu_baseline leg: 64 users per oracle block, one block per
+    # host thread per step; each step's users are drawn before its timer starts.
+    sample = min(64 * threads, cfg["n"])
     times = []
     for step in range(args.warmup + args.steps):
-        u0 = (step * sample) % max(1, W.n - sample)
+        u0 = (step * sample) % max(1, cfg["n"] - sample + 1)
+        Ub = workloads.rows(args.workload, "U", u0, sample, **over)
         t0 = time.perf_counter()
-        tau, tid, topk = oracle.kmips(W.U[u0:u0 + sample], W.P, W.k, block=32, threads=threads)
-        oracle.scores_histogram(topk, W.m)
+        tau, tid, topk = oracle.kmips(Ub, P, cfg["k"], block=64, threads=threads)
+        oracle.scores_histogram(topk, P.shape[0])
         dt = time.perf_counter() - t0
         if step >= args.warmup:
             times.append(dt)
     ms = 1000 * statistics.mean(times)
-    value = sample * W.m / (ms / 1000)
+    m = P.shape[0]
+    value = sample * m / (ms / 1000)
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": args.workload, "n": W.n, "m": W.m, "d": W.d, "k": W.k, "N": W.N,
-                       "sample_users_per_step": sample},
+            "config": {"workload": args.workload, "n": cfg["n"], "m": m, "d": cfg["d"], "k": cfg["k"],
+                       "N": cfg["N"], "sample_users_per_step": sample},
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
-                             "sample": f"{sample} users x all {W.m} items per step (FP64 thresholds + histogram)"},
+                             "sample": f"{sample} users x all {m} items per step (FP64 thresholds + histogram)"},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -344,6 +359,8 @@ def run_ours(args, rank, local, world):
     P = torch.from_numpy(W.P).cuda()
     flush = torch.empty(512 << 20, dtype=torch.uint8, device="cuda")
     ctx = rkm.Context(args.precision, device=local, profile=True, scores_from_topk=args.scores == "histogram")
+    # The result every other path must reproduce bit for bit (top-N, tau_u, t_u).
+    ref_out = [x.cpu() for x in ctx.topn(U, P, W.k, W.N, return_thresholds=True)]
     for _ in range(args.warmup):
         ctx.topn(U, P, W.k, W.N)
     torch.cuda.synchronize()
@@ -395,6 +412,13 @@ def run_ours(args, rank, local, world):
         e2e = {"value": world * pairs / e2e_s, "unit": UNIT, "ms_per_step": 1000 * e2e_s,
                "h2d_bytes_per_step": int(W.U.nbytes + W.P.nbytes), "d2h_bytes_per_step": int(8 * W.N),
                "api": "rkm_topn_host"}
+    ctx.close()
+
+    # The same inputs through the other precision paths: identical integer results (asserted)
+    # and the step-time ratios (the guarded paths against the plain exact FP32 path).
+    compare = None
+    if not args.no_compare:
+        compare = compare_paths(args, rkm, U, P, W, ref_out, local, statistics.mean(step_ms), flush)
 
     if rank != 0:
         return
@@ -406,12 +430,15 @@ def run_ours(args, rank, local, world):
     flops = 2.0 * W.n * W.m * W.d / max(1.0, launches_per_call)
     achieved = flops / (thr_avg / 1000) / 1e12
     if args.precision in ("bf16", "fp8"):
-        peak, src = tensor_peak(peaks, args.precision)
+        # The steps run back to back for seconds, so the kernel is timed inside a long run:
+        # the sustained peak is the denominator; the burst fraction is reported beside it.
+        peak, src = tensor_peak(peaks, args.precision, sustained=True)
+        burst, _ = tensor_peak(peaks, args.precision)
         roof = {"bound": "tensor", "kernel": "k_threshold_tc (threshold product + selector)",
                 "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
                 "traffic": threshold_traffic(args.workload) if not (args.n or args.m) and args.precision == "bf16"
                 else None,
-                "peak_source": src}
+                "peak_source": src, "frac_of_burst": achieved / burst, "burst_peak": burst}
     else:
         sm_mhz = peaks.get("sm_max_mhz", 2070.0)
         peak = fp32_alu_peak_tflops(sm_mhz)
@@ -435,16 +462,57 @@ def run_ours(args, rank, local, world):
             "roofline": roof,
             "gpu_launches": int(launches),
             "clocks": clk,
-            "detail": {"band_hit_fraction": statistics.mean(band) / max(1.0, statistics.mean(evald)),
+            "detail": {"band_hit_fraction": (statistics.mean(band) / max(1.0, statistics.mean(evald) - W.n * W.m)
+                                             if args.scores == "count" else None),
+                       "band_hit_fraction_of": "counting-pass pairs (evaluated pairs minus the threshold pass's n*m)",
                        "candidates_per_user": statistics.mean(cand) / W.n,
                        "items_counted_mean": statistics.mean(counted), "candidates_mean": statistics.mean(cand),
                        "band_pairs_mean": statistics.mean(band), "pairs_evaluated_mean": statistics.mean(evald),
                        "retries_last_step": st["retries"], "phase_ms_last_step": st["phase_ms"]}}
     if e2e:
         line["e2e"] = e2e
+    if compare:
+        line["detail"]["paths"] = compare
     if not args.no_cpu_baseline and world == 1:
         line["cpu_baseline"] = cpu_baseline(W, args.workload, args.cpu_seconds, args.n, args.m)
     print(json.dumps(line), flush=True)
+
+
+def compare_paths(args, rkm, U, P, W, ref_out, local, main_ms, flush):
+    """Run the workload through every other precision path: one untimed call (workspace
+    growth), one timed call.  Each result must equal the main path's top-N ids and scores,
+    tau_u and t_u exactly; a mismatch stops the benchmark."""
+    import torch
+    out = {args.precision: {"ms_per_step": main_ms}}
+    stream = torch.cuda.current_stream()
+    for prec in ("bf16", "fp8", "fp32"):
+        if prec == args.precision:
+            continue
+        with rkm.Context(prec, device=local, profile=True, scores_from_topk=args.scores == "histogram") as c:
+            c.topn(U, P, W.k, W.N)
+            torch.cuda.synchronize()
+            flush.zero_()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            res = c.topn(U, P, W.k, W.N, return_thresholds=True)
+            e1.record(stream)
+            e1.synchronize()
+            ms = e0.elapsed_time(e1)
+            st = c.stats()
+        res = [x.cpu() for x in res]
+        names = ("top-N ids", "top-N scores", "tau", "tid")
+        for name, a, b in zip(names, res, ref_out):
+            if not torch.equal(a, b):
+                raise SystemExit(f"bench: the {prec} path's {name} differ from the {args.precision} path's")
+        counting = st["pairs_evaluated"] - W.n * W.m
+        out[prec] = {"ms_per_step": ms, "identical_results": True,
+                     "phase_ms": st["phase_ms"], "candidates_per_user": st["candidates"] / W.n,
+                     "band_hit_fraction": st["band_pairs"] / max(1, counting) if args.scores == "count" else None}
+    if "fp32" in out and args.precision != "fp32":
+        out["speedup_vs_fp32"] = {p: out["fp32"]["ms_per_step"] / v["ms_per_step"]
+                                  for p, v in out.items() if p in ("bf16", "fp8")}
+    return out
 
 
 def run_batch(args, rank, local, world):

@@ -187,6 +187,21 @@ def make(name: str, **override) -> Workload:
     return mf(**cfg)
 
 
+def rows(name: str, which: str, row0: int = 0, count: int | None = None, **override) -> np.ndarray:
+    """Rows row0 .. row0+count-1 of the users ("U") or items ("P") of a named workload,
+    generated on their own (the same bytes as slicing make(name)); for the MF-like
+    workloads only those rows are drawn."""
+    cfg = dict(CONFIGS[name])
+    cfg.update(override)
+    total = cfg["n"] if which == "U" else cfg["m"]
+    count = total - row0 if count is None else min(count, total - row0)
+    if cfg["kind"] == "plain":
+        W = make(name, **override)
+        return (W.U if which == "U" else W.P)[row0:row0 + count]
+    tag, sigma = (TAG_USERS, 0.3) if which == "U" else (TAG_ITEMS, 0.5)
+    return mf_like(count, cfg["d"], cfg["seed"], tag, sigma, row0=row0)
+
+
 def batching_instances(count: int = 64, base_seed: int = 1000) -> list[dict]:
     """Sizes of the multi-instance batch: users log-uniform in [1e4, 1e6], items
     log-uniform in [5e3, 2e5], d in {32, 64, 128}, k in {5, 10, 25}, N = 20."""
