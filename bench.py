@@ -52,6 +52,8 @@ def parse():
                          " path), or the histogram of the exact S_k(u) lists of the threshold pass")
     ap.add_argument("--no-compare", action="store_true",
                     help="skip the FP8 and FP32 runs on the same inputs (identical results, speedups)")
+    ap.add_argument("--epilogue-groups", type=int, default=0, choices=[0, 2, 4],
+                    help="warpgroups reading each accumulator tile in the tensor-core kernels (0 = auto)")
     ap.add_argument("--requests", type=int, default=2000, help="serve-1m: requests per offered load")
     ap.add_argument("--slots", type=int, default=2, help="serve-1m: concurrent batches of the serving loop")
     return ap.parse_args()
@@ -358,7 +360,8 @@ def run_ours(args, rank, local, world):
     U = torch.from_numpy(W.U).cuda()
     P = torch.from_numpy(W.P).cuda()
     flush = torch.empty(512 << 20, dtype=torch.uint8, device="cuda")
-    ctx = rkm.Context(args.precision, device=local, profile=True, scores_from_topk=args.scores == "histogram")
+    ctx = rkm.Context(args.precision, device=local, profile=True, scores_from_topk=args.scores == "histogram",
+                      epilogue_groups=args.epilogue_groups)
     # The result every other path must reproduce bit for bit (top-N, tau_u, t_u).
     ref_out = [x.cpu() for x in ctx.topn(U, P, W.k, W.N, return_thresholds=True)]
     for _ in range(args.warmup):
@@ -488,7 +491,8 @@ def compare_paths(args, rkm, U, P, W, ref_out, local, main_ms, flush):
     for prec in ("bf16", "fp8", "fp32"):
         if prec == args.precision:
             continue
-        with rkm.Context(prec, device=local, profile=True, scores_from_topk=args.scores == "histogram") as c:
+        with rkm.Context(prec, device=local, profile=True, scores_from_topk=args.scores == "histogram",
+                         epilogue_groups=args.epilogue_groups) as c:
             c.topn(U, P, W.k, W.N)
             torch.cuda.synchronize()
             flush.zero_()

@@ -30,8 +30,15 @@
  *    after its results are complete (each call reads back a device status
  *    word, so it synchronises `stream` once, or twice after a retry).
  *  - The context owns its scratch memory (device workspace grown on demand
- *    and kept until rkm_destroy).  A context is not thread-safe: use one
- *    context per host thread; distinct contexts are independent.
+ *    and kept until rkm_destroy).  Calls on one context are thread-safe: a
+ *    mutex inside the context serialises calls made from several host
+ *    threads (for concurrency, give each thread its own context); distinct
+ *    contexts are independent.  rkm_destroy must not race with other calls
+ *    on the same context.
+ *  - Inputs are not required to lie on the 2^-12 grid.  Each call detects
+ *    whether they do (a device flag set while the rows are prepared) and
+ *    picks the exact integer rescoring for grid inputs, the FP64 one
+ *    otherwise; rkm_stats.exact_integer_path reports which ran.
  *  - Errors never trap on the device.  A call returns a status code and
  *    rkm_last_error() describes it.  On error the outputs are unspecified.
  */
@@ -62,7 +69,8 @@ typedef enum {
     RKM_ETIMEOUT = 5,   /* a bounded device wait gave up                        */
     RKM_ESTATE = 6,     /* call out of order (e.g. query before resident set)   */
     RKM_EINTERNAL = 7,  /* a device-side consistency check failed               */
-    RKM_EBUSY = 8       /* serving: the request queue is full; submit again later */
+    RKM_EBUSY = 8,      /* serving: the request queue is full; submit again later */
+    RKM_EIO = 9         /* a state file could not be written or read, or is corrupt */
 } rkm_status;
 
 typedef enum {
@@ -88,6 +96,13 @@ typedef struct {
                                 lists of the threshold pass (the first Section 2.2
                                 baseline: n*k increments, no counting pass and no Eq. 2
                                 filter); 0 = counting pass with the filter (default)    */
+    int epilogue_groups;     /* tensor-core product kernels: warpgroups that read each
+                                accumulator tile back (0 = auto, 2, or 4: four split every
+                                tile's columns between two groups, doubling the reads in
+                                flight).  Auto: 2 for the threshold pass; for the counting
+                                pass 4 when a tile is one K-block deep (BF16 d <= 64, FP8
+                                d <= 128), else 2.  The threshold pass takes 4 only when
+                                asked and four per-user heaps of k bounds fit (k <= 32).   */
 } rkm_opts;
 
 /* Phases timed when rkm_opts.profile is set (indices of rkm_stats.phase_ms). */
@@ -202,6 +217,33 @@ RKM_API rkm_status rkm_item_bounds(rkm_ctx* ctx, const float* U, int64_t n, int6
                            const double* tau, int32_t* uscore, void* stream);
 
 /*
+ * Guard-band check -- the approximate products of the context's tensor-core path and their
+ * error bounds, for validating the bound that makes the guarded paths exact (the paper's
+ * algorithms are exact on the CPU and have no counterpart).  For every user u and item i,
+ *   v[u * ldo + i] = the product the threshold and counting kernels compute for (u, i):
+ *                    BF16 or FP8 e4m3 operands (FP8 scaled by powers of two per user row and
+ *                    per 256-item tile of the norm-sorted items, then descaled), same TMA
+ *                    boxes, swizzle, tcgen05 MMA shape and FP32 accumulation;
+ *   E[u * ldo + i] = the bound E those kernels use for that pair, so that |v - u.p| <= E
+ *                    must hold for every pair.
+ *   U: device n x d (stride ldu), 0 <= n <= 65536; P: device m x d (stride ldp),
+ *   0 <= m <= 2^20; v, E: device [n * ldo] float, ldo >= m.  RKM_EINVAL on the FP32 path.
+ */
+RKM_API rkm_status rkm_debug_products(rkm_ctx* ctx, const float* U, int64_t n, int64_t ldu,
+                                      const float* P, int64_t m, int64_t ldp, int d,
+                                      float* v, float* E, int64_t ldo, void* stream);
+
+/*
+ * Timeout-path check (no counterpart in the paper; a library service for failure handling).
+ * Every wait inside this library's kernels gives up after a bounded number of SM clocks,
+ * records the timeout in the context's status word and lets the kernel return, so a stalled
+ * wait never hangs the device.  This call runs that bounded wait, with a limit of
+ * `wait_cycles` clocks (1 <= wait_cycles <= 2^32), on a barrier that nothing completes: it
+ * returns RKM_ETIMEOUT, and the context remains usable for later calls.
+ */
+RKM_API rkm_status rkm_debug_wait_timeout(rkm_ctx* ctx, int64_t wait_cycles, void* stream);
+
+/*
  * Serving -- keep users and their thresholds resident, then score new
  * candidate items (Definition 2 for an item whose id exceeds every catalogue
  * id, so a tie at tau_u does not make it a member; the catalogue and the
@@ -215,6 +257,20 @@ RKM_API rkm_status rkm_resident_set(rkm_ctx* ctx, const float* U, int64_t n, int
  *   counts[j] = #{u : u.Q_j > tau_u}.  Returns RKM_ESTATE without a resident set. */
 RKM_API rkm_status rkm_query_new_items(rkm_ctx* ctx, const float* Q, int64_t q, int64_t ldq,
                                int32_t* counts, void* stream);
+
+/*
+ * Serving state on disk: the resident users and their thresholds (U, tau, tid as given to
+ * rkm_resident_set), so that a serving process can restart without the threshold pass (the
+ * paper's pre-processing is done once and reused, Section 4).  The file holds a header, the
+ * three arrays and an FNV-1a hash of them; loading recomputes everything derived from them
+ * (norms, grid codes, ratio order, operand packs) exactly as rkm_resident_set does.
+ * rkm_state_save: RKM_ESTATE without a resident set, RKM_EIO when the file cannot be written.
+ * rkm_state_load: replaces the context's resident set; RKM_EIO when the file cannot be read,
+ * is not a state file, is truncated or fails its hash (the resident set is then unchanged);
+ * RKM_ESTATE while a serving loop uses the context.  Synchronises `stream`.
+ */
+RKM_API rkm_status rkm_state_save(const rkm_ctx* ctx, const char* path);
+RKM_API rkm_status rkm_state_load(rkm_ctx* ctx, const char* path, void* stream);
 
 /* Counters of the last call. */
 RKM_API rkm_status rkm_get_stats(const rkm_ctx* ctx, rkm_stats* out);
@@ -249,13 +305,16 @@ RKM_API rkm_status rkm_topn_batch(rkm_ctx* ctx, const rkm_instance* inst, int co
  * this is a library service).  For callers that cannot call cudaMalloc -- a process that
  * reserves all device memory up front and forbids later allocations, or code that runs
  * inside another library's memory manager with only the buffers it was given.
- *   scores: device [m] int32 (e.g. from rkm_scores), 1 <= m < 2^31.
+ *   scores: device [m] int32 (e.g. from rkm_scores), 1 <= m < 2^31; any int32 value,
+ *   negative ones included, orders as a signed integer.
  *   ids, top_scores: device [N] int32, filled in order (score descending, id ascending),
  *   1 <= N <= min(m, 4096); a larger N returns RKM_EINVAL.
  * No context: the only scratch is a fixed 32 KB device array inside the library (one per
  * device that loads it, kept until the process exits); nothing is allocated or freed.  The
  * first call on a device looks up that array's address (a runtime call), so make it before
- * any stream capture on that device.  Every call shares the array and clears what it needs;
+ * any stream capture on that device; the address is kept for the life of the process, so the
+ * library must not be used on a device across a device reset.  Every call shares the array
+ * and clears what it needs;
  * calls that overlap on the GPU race on it and must be serialised by the caller.  The call
  * synchronises `stream` to read its status word.
  */

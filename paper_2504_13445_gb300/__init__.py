@@ -18,12 +18,13 @@ LIB_PATH = os.path.join(HERE, "lib", "librkm.so")
 RKM_FP32, RKM_BF16, RKM_FP8 = 0, 1, 2
 PRECISIONS = {"fp32": RKM_FP32, "bf16": RKM_BF16, "fp8": RKM_FP8}
 STATUS = {0: "RKM_OK", 1: "RKM_EINVAL", 2: "RKM_ENOMEM", 3: "RKM_ECUDA", 4: "RKM_EOVERFLOW",
-          5: "RKM_ETIMEOUT", 6: "RKM_ESTATE", 7: "RKM_EINTERNAL", 8: "RKM_EBUSY"}
+          5: "RKM_ETIMEOUT", 6: "RKM_ESTATE", 7: "RKM_EINTERNAL", 8: "RKM_EBUSY", 9: "RKM_EIO"}
 
 EXPORTED = ["rkm_default_opts", "rkm_create", "rkm_destroy", "rkm_last_error", "rkm_version",
             "rkm_thresholds", "rkm_scores", "rkm_topn", "rkm_topn_host", "rkm_item_bounds",
             "rkm_resident_set", "rkm_query_new_items", "rkm_get_stats", "rkm_topn_scores_noalloc",
-            "rkm_topn_batch", "rkm_topn_from_topk", "rkm_serve_default_opts", "rkm_serve_create", "rkm_serve_submit",
+            "rkm_topn_batch", "rkm_topn_from_topk", "rkm_debug_products", "rkm_debug_wait_timeout",
+            "rkm_state_save", "rkm_state_load", "rkm_serve_default_opts", "rkm_serve_create", "rkm_serve_submit",
             "rkm_serve_wait", "rkm_serve_drain", "rkm_serve_get_stats", "rkm_serve_reset_stats",
             "rkm_serve_destroy"]
 
@@ -37,7 +38,8 @@ class RkmError(RuntimeError):
 class Opts(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int), ("k_max", ctypes.c_int), ("cand_capacity", ctypes.c_int),
                 ("band_capacity", ctypes.c_int64), ("filter", ctypes.c_int), ("profile", ctypes.c_int),
-                ("autotune", ctypes.c_int), ("tune_cache", ctypes.c_char_p), ("scores_from_topk", ctypes.c_int)]
+                ("autotune", ctypes.c_int), ("tune_cache", ctypes.c_char_p), ("scores_from_topk", ctypes.c_int),
+                ("epilogue_groups", ctypes.c_int)]
 
 
 class Instance(ctypes.Structure):
@@ -110,6 +112,10 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         "rkm_topn_scores_noalloc": (I, [P, I64, I, P, P, P]),
         "rkm_topn_batch": (I, [P, ctypes.POINTER(Instance), I, P]),
         "rkm_topn_from_topk": (I, [P, P, I64, I, I, I64, I, P, P, P]),
+        "rkm_debug_products": (I, [P, P, I64, I64, P, I64, I64, I, P, P, I64, P]),
+        "rkm_debug_wait_timeout": (I, [P, I64, P]),
+        "rkm_state_save": (I, [P, ctypes.c_char_p]),
+        "rkm_state_load": (I, [P, ctypes.c_char_p, P]),
         "rkm_serve_default_opts": (V, [ctypes.POINTER(ServeOpts)]),
         "rkm_serve_create": (I, [ctypes.POINTER(P), P, ctypes.POINTER(ServeOpts)]),
         "rkm_serve_submit": (I, [P, P, I64, I64, P, ctypes.POINTER(ctypes.c_uint64)]),
@@ -155,7 +161,8 @@ def _mat(X):
 
 def rkm_create(precision: str = "bf16", device: int = 0, k_max: int = 64, cand_capacity: int = 0,
                band_capacity: int = 0, filter: bool = True, profile: bool = False, autotune: bool = False,
-               tune_cache: str | None = None, scores_from_topk: bool = False) -> ctypes.c_void_p:
+               tune_cache: str | None = None, scores_from_topk: bool = False,
+               epilogue_groups: int = 0) -> ctypes.c_void_p:
     lib = load_library()
     o = Opts()
     lib.rkm_default_opts(ctypes.byref(o))
@@ -168,6 +175,7 @@ def rkm_create(precision: str = "bf16", device: int = 0, k_max: int = 64, cand_c
     o.autotune = 1 if autotune else 0
     o.tune_cache = tune_cache.encode() if tune_cache else None
     o.scores_from_topk = 1 if scores_from_topk else 0
+    o.epilogue_groups = epilogue_groups
     h = ctypes.c_void_p()
     _check(lib.rkm_create(ctypes.byref(h), ctypes.byref(o), device))
     return h
@@ -251,6 +259,14 @@ def rkm_query_new_items(ctx, Q):
     return counts
 
 
+def rkm_state_save(ctx, path: str) -> None:
+    _check(load_library().rkm_state_save(ctx, os.fsencode(path)))
+
+
+def rkm_state_load(ctx, path: str) -> None:
+    _check(load_library().rkm_state_load(ctx, os.fsencode(path), _stream()))
+
+
 def rkm_get_stats(ctx) -> dict:
     s = Stats()
     _check(load_library().rkm_get_stats(ctx, ctypes.byref(s)))
@@ -289,6 +305,25 @@ def rkm_topn_from_topk(ctx, lists, m: int, k: int, N: int):
     sc = torch.empty(N, dtype=torch.int32, device=lists.device)
     _check(load_library().rkm_topn_from_topk(ctx, _ptr(lists), n, kmax, k, m, N, _ptr(ids), _ptr(sc), _stream()))
     return ids, sc
+
+
+def rkm_debug_products(ctx, U, P):
+    """Approximate products of the context's tensor-core path and their error bounds:
+    returns (v [n, m] float32, E [n, m] float32) with |v - u.p| <= E required for every pair."""
+    import torch
+    U, n, ldu = _mat(U)
+    P, m, ldp = _mat(P)
+    v = torch.empty((n, m), dtype=torch.float32, device=U.device)
+    E = torch.empty((n, m), dtype=torch.float32, device=U.device)
+    _check(load_library().rkm_debug_products(ctx, _ptr(U), n, ldu, _ptr(P), m, ldp, U.shape[1], _ptr(v), _ptr(E),
+                                             m, _stream()))
+    return v, E
+
+
+def rkm_debug_wait_timeout(ctx, wait_cycles: int) -> None:
+    """Run the kernels' bounded wait on a barrier nothing completes; raises RkmError
+    (RKM_ETIMEOUT) when the wait gives up as it must."""
+    _check(load_library().rkm_debug_wait_timeout(ctx, wait_cycles, _stream()))
 
 
 def rkm_topn_scores_noalloc(scores, N: int):
@@ -416,6 +451,15 @@ class Context:
 
     def query_new_items(self, Q):
         return rkm_query_new_items(self.handle, Q)
+
+    def state_save(self, path):
+        rkm_state_save(self.handle, path)
+
+    def state_load(self, path):
+        rkm_state_load(self.handle, path)
+
+    def debug_products(self, U, P):
+        return rkm_debug_products(self.handle, U, P)
 
     def stats(self) -> dict:
         return rkm_get_stats(self.handle)

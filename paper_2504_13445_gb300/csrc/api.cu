@@ -9,6 +9,7 @@
 //                  items left before the cut, K7 over every counted item.
 // Serving:         resident users + K4 once; per query batch K1 -> K5 -> K6.
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include <algorithm>
 #include <cstdarg>
@@ -20,6 +21,7 @@
 #include <vector>
 #include <atomic>
 #include <map>
+#include <mutex>
 #include <fstream>
 #include <sstream>
 
@@ -27,6 +29,7 @@
 #include "common.cuh"
 #include "internal.h"
 #include "kernels.h"
+#include "state_io.h"
 #include "tmap.h"
 
 using rkm::TmapPair;
@@ -79,6 +82,9 @@ int64_t round_up(int64_t x, int64_t r) { return (x + r - 1) / r * r; }
 }  // namespace
 
 struct rkm_ctx {
+    // Serialises the calls made on this context from different host threads (a call that
+    // enters another entry point on the same context re-locks it).
+    mutable std::recursive_mutex mu;
     int device = 0;
     int num_sms = 0;
     rkm_opts opts{};
@@ -238,19 +244,36 @@ struct rkm_ctx {
 
 namespace {
 
-// Records CUDA events around one phase on the call's stream when profiling is on.
+// Holds a context's call mutex for the duration of an entry point (nothing for NULL).
+struct CtxLock {
+    std::unique_lock<std::recursive_mutex> lk;
+    explicit CtxLock(const rkm_ctx* c) {
+        if (c) lk = std::unique_lock<std::recursive_mutex>(c->mu);
+    }
+};
+
+// Names of the phases in NVTX ranges (indices RKM_PHASE_*).
+const char* const PHASE_NAMES[RKM_PHASES] = {"rkm prep (K1)",   "rkm threshold (K2)", "rkm exact tau (K3)",
+                                             "rkm bounds (K4)", "rkm count (K5)",     "rkm band (K6)",
+                                             "rkm top-N (K7)",  "rkm other"};
+
+// One phase of a call: an NVTX range on the host thread (seen by Nsight tools when they are
+// attached; a no-op otherwise), and CUDA events around it on the call's stream when
+// profiling is on.
 struct Phase {
     rkm_ctx* c;
     cudaStream_t s;
     int ph;
     cudaEvent_t e0 = nullptr;
     Phase(rkm_ctx* c_, cudaStream_t s_, int ph_) : c(c_), s(s_), ph(ph_) {
+        nvtxRangePushA(PHASE_NAMES[ph]);
         if (c->opts.profile) {
             e0 = c->take_event();
             cudaEventRecord(e0, s);
         }
     }
     ~Phase() {
+        nvtxRangePop();
         if (c->opts.profile) {
             cudaEvent_t e1 = c->take_event();
             cudaEventRecord(e1, s);
@@ -304,9 +327,13 @@ struct PathShape {
 // sum and the exact value for off-grid inputs; eabs covers FP32 underflow of products.
 // FP8 e4m3 products are exact (4-bit significands), but the internal accumulation of
 // kind::f8f6f4 is not documented either; FP8 accumulation on the previous generation kept
-// only about 14 bits (DeepSeek-AI, "DeepSeek-V3 Technical Report", 2024, Section 3.3), so
-// cacc = 2^-8 (64 times that) plus the FP32 term above.  The FP8 representation error
-// (3 mantissa bits, ||x^ - x|| near 2^-5 ||x||) dominates the band anyway.
+// only about 14 bits (DeepSeek-AI, "DeepSeek-V3 Technical Report", 2024, Section 3.3).
+// Measured on GB300 through rkm_debug_products, on operands that e4m3 represents exactly
+// (so the accumulation is the only error) with partial sums spanning more than 24 bits, the
+// largest error of kind::f8f6f4 was 1.1 * 2^-24 ||u|| ||p|| at d = 128 and 256: FP32-like, no
+// narrow accumulator.  So FP8 takes the BF16 constant, cacc = d 2^-22, which is still about
+// 100 times the largest error measured at d = 128.  The FP8 representation error (3 mantissa
+// bits, ||x^ - x|| near 2^-5 ||x||) dominates the band anyway.
 PathShape path_shape(rkm_precision prec, int d) {
     PathShape ps{};
     const double dd = (double)d;
@@ -323,7 +350,7 @@ PathShape path_shape(rkm_precision prec, int d) {
         ps.elem_bytes = 1;
         ps.item_tile = BI_TC;
         ps.dp = (int)round_up(d, 128);
-        ps.cacc = (float)((0x1p-8 + dd * 0x1p-22 + dd * 0x1p-50) * (1.0 + 0x1p-20));
+        ps.cacc = (float)((dd * 0x1p-22 + dd * 0x1p-50) * (1.0 + 0x1p-20));
     } else {
         ps.tc = true;
         ps.elem_bytes = 2;
@@ -492,15 +519,23 @@ struct ThrPlan {
     int nseg, cap;
 };
 
+// Candidate segments per user of a threshold launch with the largest k `kheap` (one per
+// epilogue warpgroup of the tensor-core kernel; one on the FP32 path).  want_groups: the
+// context's epilogue_groups option (0 = auto).
+int threshold_segments(const PathShape& ps, int kheap, int want_groups) {
+    return ps.tc ? threshold_groups(kheap, ps.dp, ps.fp8, want_groups) : 1;
+}
+
+// nseg: candidate segments of the launch this problem joins (0 = a launch of its own).
 rkm_status threshold_prepare(rkm_ctx* c, const PathShape& ps, const float* U, int64_t n, int64_t ldu, int d, int k,
-                             const RowPrep& up, const ItemSide& it, ThrPlan* pl, cudaStream_t s) {
+                             const RowPrep& up, const ItemSide& it, ThrPlan* pl, cudaStream_t s, int nseg = 0) {
     pl->n_pad = round_up(std::max<int64_t>(n, 1), BU);
     {
         Phase ph(c, s, RKM_PHASE_PREP);
         TRY(pack(c, ps, U, n, ldu, d, nullptr, pl->n_pad, c->u_pack, &pl->apack, s, up.e));
     }
     pl->cap = c->cand_cap;
-    pl->nseg = ps.tc ? 2 : 1;
+    pl->nseg = nseg > 0 ? nseg : threshold_segments(ps, k, c->opts.epilogue_groups);
     TRY(c->ensure(c->cand, n * (int64_t)pl->nseg * pl->cap, &pl->cand));
     TRY(c->ensure(c->cand_cnt, n * (int64_t)pl->nseg, &pl->cand_cnt));
     TRY(c->ensure(c->lfin, n, &pl->lfin));
@@ -556,7 +591,7 @@ rkm_status threshold_launch_one(rkm_ctx* c, const PathShape& ps, const ThrPlan& 
         TRY(c->instances(1, &hi, &di));
         TRY(threshold_descriptor(ps, pl, it, hi));
         CUDA_TRY(cudaMemcpyAsync(di, hi, sizeof(TcInstance), cudaMemcpyHostToDevice, s));
-        launch_threshold_tc(di, 1, (pl.a.n + BU - 1) / BU, pl.a.k, ps.dp, ps.fp8, c->num_sms, s);
+        launch_threshold_tc(di, 1, (pl.a.n + BU - 1) / BU, pl.a.k, ps.dp, ps.fp8, pl.nseg, c->num_sms, s);
     } else {
         launch_threshold_simt(pl.a, s);
     }
@@ -606,7 +641,7 @@ rkm_status thresholds_core(rkm_ctx* c, const PathShape& ps, const float* U, int6
                            const float* P, int64_t ldp, int d, int k, const RowPrep& up, const ItemSide& it,
                            double* tau, int* tid, int* topk, cudaStream_t s) {
     for (int attempt = 0;; ++attempt) {
-        const int64_t per_user = (int64_t)(ps.tc ? 2 : 1) * c->cand_cap * 20;
+        const int64_t per_user = (int64_t)threshold_segments(ps, k, c->opts.epilogue_groups) * c->cand_cap * 20;
         const int64_t slice = std::min<int64_t>(n, std::max<int64_t>(BU, candidate_budget(c) / per_user / BU * BU));
         bool overflow = false;
         for (int64_t u0 = 0; u0 < n && !overflow; u0 += slice) {
@@ -696,6 +731,7 @@ rkm_status count_stage(rkm_ctx* c, const PathShape& ps, int64_t n, const UserOrd
     a.unit_off = unit_off;
     a.t_begin = t_begin;
     a.group = group;
+    a.groups = count_groups(ps.dp, ps.fp8, c->opts.epilogue_groups);
     a.cacc = ps.cacc;
     a.eabs = ps.eabs;
     a.counts = cnt;
@@ -833,6 +869,7 @@ void rkm_default_opts(rkm_opts* o) {
     o->autotune = 0;
     o->tune_cache = nullptr;
     o->scores_from_topk = 0;
+    o->epilogue_groups = 0;
 }
 
 const char* rkm_last_error(void) { return g_err.c_str(); }
@@ -847,6 +884,8 @@ rkm_status rkm_create(rkm_ctx** out, const rkm_opts* opts, int device) {
     if (opts) o = *opts;
     if (o.k_max < 1 || o.k_max > KMAX) return fail(RKM_EINVAL, "k_max must be in [1, %d]", KMAX);
     if (o.precision < RKM_FP32 || o.precision > RKM_FP8) return fail(RKM_EINVAL, "unknown precision");
+    if (o.epilogue_groups != 0 && o.epilogue_groups != 2 && o.epilogue_groups != 4)
+        return fail(RKM_EINVAL, "epilogue_groups must be 0, 2 or 4");
     if (o.cand_capacity < 0 || o.band_capacity < 0) return fail(RKM_EINVAL, "negative capacity");
     int ndev = 0;
     CUDA_TRY(cudaGetDeviceCount(&ndev));
@@ -887,6 +926,7 @@ void rkm_destroy(rkm_ctx* c) {
 }
 
 rkm_status rkm_get_stats(const rkm_ctx* c, rkm_stats* out) {
+    CtxLock lock_(c);
     if (!c || !out) return fail(RKM_EINVAL, "null argument");
     *out = c->stats;
     return RKM_OK;
@@ -894,6 +934,7 @@ rkm_status rkm_get_stats(const rkm_ctx* c, rkm_stats* out) {
 
 rkm_status rkm_thresholds(rkm_ctx* c, const float* U, int64_t n, int64_t ldu, const float* P, int64_t m,
                           int64_t ldp, int d, int k, double* tau, int32_t* tid, int32_t* topk, void* stream) {
+    CtxLock lock_(c);
     TRY(check_common(c, d));
     TRY(check_matrix(U, n, ldu, d, "U"));
     TRY(check_matrix(P, m, ldp, d, "P"));
@@ -1020,6 +1061,7 @@ static rkm_status scores_impl(rkm_ctx* c, const PathShape& ps, const float* U, i
 
 rkm_status rkm_scores(rkm_ctx* c, const float* U, int64_t n, int64_t ldu, const float* P, int64_t m, int64_t ldp,
                       int d, const double* tau, const int32_t* tid, int32_t* scores, void* stream) {
+    CtxLock lock_(c);
     TRY(check_common(c, d));
     TRY(check_matrix(U, n, ldu, d, "U"));
     TRY(check_matrix(P, m, ldp, d, "P"));
@@ -1054,6 +1096,7 @@ rkm_status rkm_scores(rkm_ctx* c, const float* U, int64_t n, int64_t ldu, const 
 rkm_status rkm_topn(rkm_ctx* c, const float* U, int64_t n, int64_t ldu, const float* P, int64_t m, int64_t ldp,
                     int d, int k, int N, int32_t* ids, int32_t* top_scores, double* tau_out, int32_t* tid_out,
                     void* stream) {
+    CtxLock lock_(c);
     TRY(check_common(c, d));
     TRY(check_matrix(U, n, ldu, d, "U"));
     TRY(check_matrix(P, m, ldp, d, "P"));
@@ -1125,6 +1168,7 @@ rkm_status rkm_topn(rkm_ctx* c, const float* U, int64_t n, int64_t ldu, const fl
 
 rkm_status rkm_topn_from_topk(rkm_ctx* c, const int32_t* lists, int64_t n, int kmax, int k, int64_t m, int N,
                               int32_t* ids, int32_t* top_scores, void* stream) {
+    CtxLock lock_(c);
     if (!c) return fail(RKM_EINVAL, "null context");
     if (n < 0 || n > (int64_t)INT32_MAX) return fail(RKM_EINVAL, "n must be in [0, 2^31-1]");
     if (n > 0 && !lists) return fail(RKM_EINVAL, "null lists");
@@ -1159,6 +1203,7 @@ rkm_status rkm_topn_from_topk(rkm_ctx* c, const int32_t* lists, int64_t n, int k
 
 rkm_status rkm_topn_host(rkm_ctx* c, const float* U, int64_t n, int64_t ldu, const float* P, int64_t m,
                          int64_t ldp, int d, int k, int N, int32_t* ids, int32_t* top_scores, void* stream) {
+    CtxLock lock_(c);
     TRY(check_common(c, d));
     TRY(check_matrix(U, n, ldu, d, "U"));
     TRY(check_matrix(P, m, ldp, d, "P"));
@@ -1182,6 +1227,7 @@ rkm_status rkm_topn_host(rkm_ctx* c, const float* U, int64_t n, int64_t ldu, con
 
 rkm_status rkm_item_bounds(rkm_ctx* c, const float* U, int64_t n, int64_t ldu, const float* P, int64_t m,
                            int64_t ldp, int d, const double* tau, int32_t* uscore, void* stream) {
+    CtxLock lock_(c);
     TRY(check_common(c, d));
     TRY(check_matrix(U, n, ldu, d, "U"));
     TRY(check_matrix(P, m, ldp, d, "P"));
@@ -1210,8 +1256,69 @@ rkm_status rkm_item_bounds(rkm_ctx* c, const float* U, int64_t n, int64_t ldu, c
     return RKM_OK;
 }
 
+rkm_status rkm_debug_products(rkm_ctx* c, const float* U, int64_t n, int64_t ldu, const float* P, int64_t m,
+                              int64_t ldp, int d, float* v, float* E, int64_t ldo, void* stream) {
+    CtxLock lock_(c);
+    TRY(check_common(c, d));
+    TRY(check_matrix(U, n, ldu, d, "U"));
+    TRY(check_matrix(P, m, ldp, d, "P"));
+    if (c->opts.precision == RKM_FP32) return fail(RKM_EINVAL, "rkm_debug_products: tensor-core paths only");
+    if (n > 65536 || m > 1048576) return fail(RKM_EINVAL, "rkm_debug_products: n <= 65536 and m <= 2^20");
+    if (ldo < m) return fail(RKM_EINVAL, "rkm_debug_products: ldo < m");
+    if (n > 0 && m > 0 && (!v || !E)) return fail(RKM_EINVAL, "null v/E");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    reset_stats(c);
+    if (n == 0 || m == 0) return RKM_OK;
+    TRY(begin_call(c, s));
+    const PathShape ps = path_shape(c->opts.precision, d);
+    RowPrep up;
+    ItemSide it;
+    TRY(prep_rows(c, ps, U, n, ldu, d, c->u_e, c->u_q, c->u_n2, c->u_nrm, c->u_nhat, c->u_del, &up, s));
+    TRY(prep_items(c, ps, P, m, ldp, d, catalogue_bufs(c), &it, s));
+    const int64_t n_pad = round_up(n, BU);
+    void* apack;
+    TRY(pack(c, ps, U, n, ldu, d, nullptr, n_pad, c->u_pack, &apack, s, up.e));
+    TmapPair tm;
+    TRY(make_tmaps(apack, n_pad, it.pack, it.m_pad, ps.dp, BI_TC, ps.elem_bytes, &tm));
+    ProductsArgs a{};
+    a.n = n;
+    a.m = m;
+    a.ldo = ldo;
+    a.dp = ps.dp;
+    a.perm = it.perm;
+    a.unrm = up.nrm;
+    a.unhat = up.nhat;
+    a.udel = up.del;
+    a.uexp = up.e;
+    a.thmax = it.thmax;
+    a.tdel = it.tdel;
+    a.texp = it.texp;
+    a.cacc = ps.cacc;
+    a.eabs = ps.eabs;
+    a.v = v;
+    a.E = E;
+    a.st = c->st;
+    launch_products_tc(a, &tm.a, &tm.b, ps.fp8, s);
+    TRY(read_status(c, s));
+    return RKM_OK;
+}
+
+rkm_status rkm_debug_wait_timeout(rkm_ctx* c, int64_t wait_cycles, void* stream) {
+    CtxLock lock_(c);
+    if (!c) return fail(RKM_EINVAL, "null context");
+    if (wait_cycles < 1 || wait_cycles > ((int64_t)1 << 32))
+        return fail(RKM_EINVAL, "wait_cycles must be in [1, 2^32]");
+    CUDA_TRY(cudaSetDevice(c->device));
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    reset_stats(c);
+    TRY(begin_call(c, s));
+    launch_wait_timeout((long long)wait_cycles, c->st, s);
+    return read_status(c, s);
+}
+
 rkm_status rkm_resident_set(rkm_ctx* c, const float* U, int64_t n, int64_t ldu, int d, const double* tau,
                             const int32_t* tid, void* stream) {
+    CtxLock lock_(c);
     TRY(check_common(c, d));
     TRY(check_matrix(U, n, ldu, d, "U"));
     if (n > 0 && (!tau || !tid)) return fail(RKM_EINVAL, "null tau/tid");
@@ -1246,7 +1353,57 @@ rkm_status rkm_resident_set(rkm_ctx* c, const float* U, int64_t n, int64_t ldu, 
     return RKM_OK;
 }
 
+rkm_status rkm_state_save(const rkm_ctx* c, const char* path) {
+    CtxLock lock_(c);
+    if (!c || !path) return fail(RKM_EINVAL, "null context or path");
+    if (!c->resident) return fail(RKM_ESTATE, "rkm_state_save before rkm_resident_set");
+    CUDA_TRY(cudaSetDevice(c->device));
+    const int64_t n = c->res_n;
+    const int d = c->res_d;
+    std::vector<float> U((size_t)n * d);
+    std::vector<double> tau((size_t)n);
+    std::vector<int32_t> tid((size_t)n);
+    if (n > 0) {
+        CUDA_TRY(cudaMemcpy(U.data(), c->res_U.p, U.size() * sizeof(float), cudaMemcpyDeviceToHost));
+        CUDA_TRY(cudaMemcpy(tau.data(), c->res_tau.p, tau.size() * sizeof(double), cudaMemcpyDeviceToHost));
+        CUDA_TRY(cudaMemcpy(tid.data(), c->res_tid.p, tid.size() * sizeof(int32_t), cudaMemcpyDeviceToHost));
+    }
+    std::string err;
+    if (!state::write(path, n, d, U.data(), tau.data(), tid.data(), &err)) return fail(RKM_EIO, "%s", err.c_str());
+    return RKM_OK;
+}
+
+rkm_status rkm_state_load(rkm_ctx* c, const char* path, void* stream) {
+    CtxLock lock_(c);
+    if (!c || !path) return fail(RKM_EINVAL, "null context or path");
+    if (c->servers.load() != 0) return fail(RKM_ESTATE, "the resident set is in use by a serving loop");
+    int64_t n = 0;
+    int d = 0;
+    std::vector<float> U;
+    std::vector<double> tau;
+    std::vector<int32_t> tid;
+    std::string err;
+    if (!state::read(path, &n, &d, &U, &tau, &tid, &err)) return fail(RKM_EIO, "%s", err.c_str());
+    CUDA_TRY(cudaSetDevice(c->device));
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    float* Ud;
+    double* taud;
+    int* tidd;
+    TRY(c->ensure(c->h_U, std::max<int64_t>(n * d, 1), &Ud));
+    TRY(c->ensure(c->tau_tmp, std::max<int64_t>(n, 1), &taud));
+    TRY(c->ensure(c->tid_tmp, std::max<int64_t>(n, 1), &tidd));
+    if (n > 0) {
+        CUDA_TRY(cudaMemcpyAsync(Ud, U.data(), U.size() * sizeof(float), cudaMemcpyHostToDevice, s));
+        CUDA_TRY(cudaMemcpyAsync(taud, tau.data(), tau.size() * sizeof(double), cudaMemcpyHostToDevice, s));
+        CUDA_TRY(cudaMemcpyAsync(tidd, tid.data(), tid.size() * sizeof(int32_t), cudaMemcpyHostToDevice, s));
+    }
+    // rkm_resident_set synchronises the stream before it returns, so the host vectors
+    // outlive the copies.
+    return rkm_resident_set(c, Ud, n, d, d, taud, tidd, stream);
+}
+
 rkm_status rkm_query_new_items(rkm_ctx* c, const float* Q, int64_t q, int64_t ldq, int32_t* counts, void* stream) {
+    CtxLock lock_(c);
     if (!c) return fail(RKM_EINVAL, "null context");
     return rkm::query_resident(c, c, Q, q, ldq, counts, static_cast<cudaStream_t>(stream));
 }
@@ -1312,6 +1469,15 @@ int64_t instance_cost(const rkm_instance& I, const PathShape& ps) {
 // launch over all instances (largest first); per instance exact rescoring, counting, top-N.
 rkm_status batch_enqueue(rkm_ctx* c, const rkm_instance* inst, int count, cudaStream_t s) {
     std::vector<InstWork> w(count);
+    // Every instance of the persistent threshold launch has one candidate segment per
+    // epilogue warpgroup of that launch, chosen for the batch's largest k and depth.
+    int kheap = 1, max_dp = 64;
+    for (int i = 0; i < count; ++i) {
+        kheap = std::max(kheap, inst[i].k);
+        max_dp = std::max(max_dp, path_shape(c->opts.precision, inst[i].d).dp);
+    }
+    const PathShape ps0 = path_shape(c->opts.precision, inst[0].d);
+    const int nseg = ps0.tc ? threshold_groups(kheap, max_dp, ps0.fp8, c->opts.epilogue_groups) : 1;
     for (int i = 0; i < count; ++i) {
         rkm_ctx* sc = c->sub[i];
         const rkm_instance& I = inst[i];
@@ -1322,7 +1488,7 @@ rkm_status batch_enqueue(rkm_ctx* c, const rkm_instance* inst, int count, cudaSt
         TRY(prep_rows(sc, x.ps, I.U, I.n, I.ldu, I.d, sc->u_e, sc->u_q, sc->u_n2, sc->u_nrm, sc->u_nhat, sc->u_del,
                       &x.up, s));
         TRY(prep_items(sc, x.ps, I.P, I.m, I.ldp, I.d, catalogue_bufs(sc), &x.it, s));
-        TRY(threshold_prepare(sc, x.ps, I.U, I.n, I.ldu, I.d, I.k, x.up, x.it, &x.pl, s));
+        TRY(threshold_prepare(sc, x.ps, I.U, I.n, I.ldu, I.d, I.k, x.up, x.it, &x.pl, s, nseg));
         TRY(sc->ensure(sc->tau_tmp, I.n, &x.tau));
         TRY(sc->ensure(sc->tid_tmp, I.n, &x.tid));
     }
@@ -1342,17 +1508,14 @@ rkm_status batch_enqueue(rkm_ctx* c, const rkm_instance* inst, int count, cudaSt
         TcInstance* dev;
         TRY(c->ensure(c->batch_dev, count, &dev));
         long long units = 0;
-        int kheap = 1, max_dp = 64;
         for (int j = 0; j < count; ++j) {
             const int i = order[j];
             TRY(threshold_descriptor(w[i].ps, w[i].pl, w[i].it, &c->batch_host[j]));
             c->batch_host[j].unit_begin = units;
             units += (inst[i].n + BU - 1) / BU;
-            kheap = std::max(kheap, inst[i].k);
-            max_dp = std::max(max_dp, w[i].ps.dp);
         }
         CUDA_TRY(cudaMemcpyAsync(dev, c->batch_host, (size_t)count * sizeof(TcInstance), cudaMemcpyHostToDevice, s));
-        launch_threshold_tc(dev, count, units, kheap, max_dp, w[0].ps.fp8, c->num_sms, s);
+        launch_threshold_tc(dev, count, units, kheap, max_dp, w[0].ps.fp8, nseg, c->num_sms, s);
     } else {
         for (int i = 0; i < count; ++i) launch_threshold_simt(w[i].pl.a, s);
     }
@@ -1460,6 +1623,7 @@ rkm_status tune_instance(rkm_ctx* sc, const rkm_instance& I, cudaStream_t s, Tun
 }  // namespace
 
 extern "C" rkm_status rkm_topn_batch(rkm_ctx* c, const rkm_instance* inst, int count, void* stream) {
+    CtxLock lock_(c);
     if (!c) return fail(RKM_EINVAL, "null context");
     if (!inst || count < 1 || count > 4096) return fail(RKM_EINVAL, "count must be in [1, 4096]");
     const double t0 = now_ms();

@@ -117,8 +117,38 @@ struct __align__(64) TcInstance {
 // array; total_units = sum of the instances' user tiles; kheap = largest k; max_dp = largest
 // padded depth (elements).  fp8: operands are e4m3 (128 per K-block) with power-of-two
 // scales, else BF16 (64 per K-block); every instance of a launch has the same kind.
+// Epilogue warpgroups (= candidate segments per user) of the tensor-core threshold launch for
+// the largest k, padded depth and operand kind of its instances.  want = 2 or 4 asks for that
+// many, 0 chooses; 4 only when four per-user heaps of kheap bounds (kheap <= 32) still leave
+// the shared-memory ring enough slots, else 2.
+int threshold_groups(int kheap, int max_dp, bool fp8, int want);
+// Epilogue warpgroups of the tensor-core counting kernel for padded depth dp (want as above).
+int count_groups(int dp, bool fp8, int want);
+// ng: epilogue warpgroups, as threshold_groups returned for these instances.
 void launch_threshold_tc(const TcInstance* inst, int count, long long total_units, int kheap, int max_dp,
-                         bool fp8, int num_sms, cudaStream_t s);
+                         bool fp8, int ng, int num_sms, cudaStream_t s);
+
+// Approximate products of the tensor-core paths with their guard band, for validating the
+// error bound: v[u * ldo + perm[pos]] = the product the threshold and counting kernels see
+// for user u and the item at sorted position pos (FP8: descaled), E[...] = its bound.
+struct ProductsArgs {
+    int64_t n, m, ldo;
+    int dp;
+    const int* perm;                      // sorted pos -> original item id
+    const float *unrm, *unhat, *udel;     // [n] user norms (as ThresholdArgs)
+    const int* uexp;                      // [n] FP8 user row exponents
+    const float *thmax, *tdel;            // [item tiles] item norm maxima
+    const int* texp;                      // [item tiles] FP8 tile exponents
+    float cacc, eabs;
+    float* v;                             // [n][ldo]
+    float* E;                             // [n][ldo]
+    DevStatus* st;
+};
+void launch_products_tc(const ProductsArgs& a, const void* tmapA, const void* tmapB, bool fp8, cudaStream_t s);
+
+// A bounded mbarrier wait (the product kernels' own) on a phase nothing completes, with a
+// limit of `limit` SM clocks: sets st->timeout and returns.
+void launch_wait_timeout(long long limit, DevStatus* st, cudaStream_t s);
 
 // ---- exact rescoring (K3, K6, K8) ---------------------------------------------------
 
@@ -168,6 +198,7 @@ struct CountArgs {
     const unsigned* unit_off;  // [tiles+1] work units per item tile, exclusive scan
     int t_begin;            // first item tile of the stage
     int group;              // user tiles per work unit
+    int groups;             // tensor-core kernel: epilogue warpgroups (2 or 4)
     float cacc, eabs;
     int* counts;            // [m] by sorted position
     int2* band; unsigned band_cap;

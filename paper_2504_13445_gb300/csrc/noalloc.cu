@@ -31,8 +31,11 @@ constexpr int NOALLOC_MAX_DEVICES = 64;
 // 32 KB per device that loads the library, held until the process exits.
 static __device__ __align__(256) unsigned long long g_topn_scratch[NOALLOC_WORDS];
 
+// The score's sign bit is flipped so that signed scores order correctly as unsigned keys
+// (a negative score sorts below every non-negative one); the top-N writer flips it back.
 __device__ __forceinline__ unsigned long long score_key(const int* scores, int64_t i) {
-    return ((unsigned long long)(unsigned)scores[i] << 32) | (unsigned long long)(0xFFFFFFFFu - (unsigned)i);
+    return ((unsigned long long)((unsigned)scores[i] ^ 0x80000000u) << 32) |
+           (unsigned long long)(0xFFFFFFFFu - (unsigned)i);
 }
 
 // Same selection as k_topn (most-significant-digit radix select over the unique keys
@@ -95,16 +98,18 @@ __global__ void __launch_bounds__(NOALLOC_THREADS) k_topn_noalloc(const int* __r
         int rank = 0;
         for (int r = 0; r < N; ++r) rank += sel[r] > key;
         ids[rank] = (int)(0xFFFFFFFFu - (unsigned)(key & 0xFFFFFFFFull));
-        top_scores[rank] = (int)(key >> 32);
+        top_scores[rank] = (int)((unsigned)(key >> 32) ^ 0x80000000u);
     }
 }
 
 std::mutex g_setup_mutex;
 unsigned long long* g_scratch_ptr[NOALLOC_MAX_DEVICES] = {};
 
-// Device address of the scratch array on the current device, looked up once per device.
-// The lookup is a runtime call, so the first call on a device should precede any stream
-// capture on that device.
+// Device address of the scratch array on the current device, looked up once per device and
+// kept for the life of the process.  The lookup is a runtime call, so the first call on a
+// device should precede any stream capture on that device.  A device reset
+// (cudaDeviceReset) reloads the library's module and moves the array: the library must not
+// be used on a device across a reset.
 cudaError_t scratch_address(int dev, unsigned long long** out) {
     std::lock_guard<std::mutex> lock(g_setup_mutex);
     if (!g_scratch_ptr[dev]) {

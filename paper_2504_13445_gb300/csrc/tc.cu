@@ -2,16 +2,19 @@
 // pass (K5): BF16 or FP8 e4m3 operands staged by TMA into 128-byte-swizzled shared memory
 // (a K-block is 128 bytes of every row: 64 BF16 or 128 FP8 values), one thread issuing
 // 128 x 256 x 16 (BF16) or 128 x 256 x 32 (FP8) MMAs into a double-buffered FP32 accumulator in TMEM
-// (2 x 256 columns), and eight epilogue warps that read the accumulator back with
-// tcgen05.ld and run the per-user epilogues of epilogue.cuh.  The user x item product
+// (2 x 256 columns), and NG epilogue warpgroups (NG = 2 or 4) that read the accumulator back
+// with tcgen05.ld and run the per-user epilogues of epilogue.cuh.  The user x item product
 // never leaves the SM.
 //
-// Roles (320 threads, one CTA per SM, persistent):
+// Roles (64 + 128 NG threads, one CTA per SM, persistent):
 //   warp 0      TMA producer: the resident operand once per work unit, then a ring of
 //               K-block slots of the streamed operand.
 //   warp 1      TMEM allocator and MMA issuer (one thread).
-//   warps 2-9   two epilogue warpgroups; group h consumes accumulator buffer h, i.e. every
-//               other product tile, so the epilogue runs two tiles at once.
+//   warps 2..   NG epilogue warpgroups.  Group g consumes accumulator buffer g % 2, i.e. every
+//               other product tile, and of each such tile the columns
+//               [(g / 2) * CW, (g / 2 + 1) * CW), CW = 512 / NG.  With NG = 4 every tile is
+//               read by eight warps at once (twice the TMEM loads in flight of NG = 2), which
+//               is what keeps the epilogue up with the MMA at small d.
 // Threshold pass: resident = 128 users, streamed = 256-item tiles.  Each warpgroup keeps
 // its own lower-bound heap per user (each is a valid lower bound of tau_u because it is the
 // k-th largest lower bound over a subset of the items); the final L_u is their maximum.
@@ -30,7 +33,8 @@ namespace rkm {
 
 namespace {
 
-constexpr int TC_THREADS = 320;
+// Threads of a product kernel with NG epilogue warpgroups.
+constexpr int tc_threads(int ng) { return 64 + 128 * ng; }
 constexpr int MAX_SLOTS = 4;
 constexpr uint32_t TMEM_COLS = 512;
 constexpr uint32_t KB_BYTES_U = 128 * 128;  // one K-block (128 bytes: 64 BF16 / 128 FP8) of 128 user rows
@@ -91,7 +95,8 @@ __device__ __forceinline__ void drain_wait(uint64_t* bar, uint32_t parity, DevSt
     }
 }
 
-__device__ __forceinline__ void setup(TcBars* B, int slots, int warp) {
+// consumers: warps that release each accumulator buffer (4 per warpgroup reading it).
+__device__ __forceinline__ void setup(TcBars* B, int slots, int warp, int consumers) {
     if (threadIdx.x == 0) {
         for (int b = 0; b < 2; ++b) {
             mbar_init(&B->res_full[b], 1);
@@ -104,7 +109,7 @@ __device__ __forceinline__ void setup(TcBars* B, int slots, int warp) {
         }
         for (int b = 0; b < 2; ++b) {
             mbar_init(&B->tfull[b], 1);
-            mbar_init(&B->tempty[b], 4);
+            mbar_init(&B->tempty[b], (uint32_t)consumers);
         }
         B->abort = 0;
         mbar_fence_init();
@@ -145,8 +150,8 @@ __device__ __forceinline__ int unit_instance(const TcInstance* inst, int count, 
 // tile) pairs numbered consecutively across the instances; CTA b takes units b, b + grid, ...
 // A unit streams every item tile of its instance, so the caller orders the instances by
 // descending cost to balance the CTAs.
-template <bool FP8>
-__global__ void __launch_bounds__(TC_THREADS, 1)
+template <bool FP8, int NG>
+__global__ void __launch_bounds__(tc_threads(NG), 1)
     k_threshold_tc(const TcInstance* __restrict__ inst, int count, long long total_units, int kheap,
                    const TcLayout L) {
     using Op = Operand<FP8>;
@@ -162,10 +167,10 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     // Running bounds published per user row by each epilogue group: Lpub[h][row], tagged with
     // the work unit (a bound of another unit is never used).  Initialised before setup's
     // barrier so that no group can read an uninitialised entry.
-    unsigned long long* Lpub = reinterpret_cast<unsigned long long*>(heaps + 2 * kheap * BU);
+    unsigned long long* Lpub = reinterpret_cast<unsigned long long*>(heaps + NG * kheap * BU);
     if (warp >= 2) Lpub[threadIdx.x - 64] = 0xFFFFFFFF00000000ull;
 
-    setup(B, S, warp);
+    setup(B, S, warp, 2 * NG);
     const uint32_t tmem = B->tmem_base;
 
     if (warp == 0) {
@@ -266,11 +271,14 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             drain_wait(&B->drain, 0u, st);
         }
     } else {
-        const int ew = warp - 2;          // 0..7
-        const int h = ew >> 2;            // warpgroup = accumulator buffer it consumes
+        constexpr int CW = 2 * BI_TC / NG;  // accumulator columns a group reads per tile
+        const int ew = warp - 2;          // 0 .. 4 NG - 1
+        const int g = ew >> 2;            // warpgroup
+        const int h = g & 1;              // accumulator buffer it consumes
+        const int cg = (g >> 1) * CW;     // its first column of each tile
         const int q = warp & 3;           // TMEM lane quarter this warp may access
         const int r = q * 32 + lane;      // user row of the tile
-        float* heap = heaps + h * (kheap * BU);
+        float* heap = heaps + g * (kheap * BU);
         uint32_t tile_j = 0;
         bool ok = true;
         for (long long w = blockIdx.x; w < total_units && ok; w += gridDim.x) {
@@ -279,7 +287,10 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             const long long ut = w - I.unit_begin;
             const int item_tiles = (int)((a.m + BI_TC - 1) / BI_TC);
             const int64_t u = ut * BU + r;
-            const bool active = u < a.n;
+            // The candidate lists have one segment per warpgroup; an instance prepared for
+            // another group count is a host bug: flag it and write nothing.
+            if (a.nseg != NG && lane == 0 && q == 0) a.st->internal_error = 1u;
+            const bool active = u < a.n && a.nseg == NG;
             for (int j = 0; j < a.k; ++j) heap[j * BU + r] = -INFINITY;
             SelState s;
             s.L = -INFINITY;
@@ -288,7 +299,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             s.Lx = -INFINITY;
             s.thr = -INFINITY;
             s.cnt = 0;
-            s.pub = &Lpub[h * BU + r];
+            s.pub = &Lpub[g * BU + r];
             s.tag = (unsigned)w;
             s.defer = 1;
             s.mark = 0;
@@ -297,7 +308,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             const float unh = active ? a.unhat[u] : 0.f;
             const float ud = active ? a.udel[u] : 0.f;
             const int ue = (FP8 && active) ? fp8_exp(a.uexp[u]) : 0;
-            Cand* mycand = a.cand + ((active ? u : 0) * a.nseg + h) * (int64_t)a.cap;
+            Cand* mycand = a.cand + ((active ? u : 0) * a.nseg + g) * (int64_t)a.cap;
             // This group's first tile of the unit, then every other one: the bound maxima of
             // the next one are loaded while the current one is processed.
             int itn = (int)((tile_j & 1u) == (uint32_t)h ? 0 : 1);
@@ -323,23 +334,27 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                 tc_fence_after();
                 const float E = err_bound(a.cacc, a.eabs, un, unh, ud, thm, tdl);
                 const float f = FP8 ? pow2i(ue + a.texp[it] - 16) : 1.f;  // descale of the FP8 product
-                // The partner's bound may be stale or from this unit's start (-inf):
-                // any value it held is a valid lower bound of tau_u for the current user.
-                s.Lx = read_bound(&Lpub[(1 - h) * BU + r], (unsigned)w);
-                const uint32_t tb = tmem + ((uint32_t)(q * 32) << 16) + b * BI_TC;
+                // The other groups' bounds may be stale or from this unit's start (-inf):
+                // any value they held is a valid lower bound of tau_u for the current user.
+                float lx = -INFINITY;
+#pragma unroll
+                for (int o = 0; o < NG; ++o)
+                    if (o != g) lx = fmaxf(lx, read_bound(&Lpub[o * BU + r], (unsigned)w));
+                s.Lx = lx;
+                const uint32_t tb = tmem + ((uint32_t)(q * 32) << 16) + b * BI_TC + cg;
                 if (!warm) {
                     // First tile of this group for these users: a lockstep first pass over the
                     // accumulator gives a lower bound before any candidate is recorded, so the
                     // heap does not fill one divergent insertion at a time: the k-th largest of
-                    // 64 maxima of 4 columns (k <= 64 distinct items reach it).  Hits of this
-                    // tile are recorded against it until the tile's end, so its tightness sets
-                    // how many candidates the first tile records.
+                    // CW / 4 maxima of 4 columns (k <= CW / 4 distinct items reach it; -inf for
+                    // a larger k).  Hits of this tile are recorded against it until the tile's
+                    // end, so its tightness sets how many candidates the first tile records.
                     auto load = [&](int c0, float (&v)[32]) {
                         __syncwarp();
                         tmem_ld32(tb + c0, v);
                         if constexpr (FP8) scale_values(v, f);
                     };
-                    const float lw = warm_bound<64, BI_TC>(load, it * BI_TC, a.m, a.k, E);
+                    const float lw = warm_bound<CW / 4, CW>(load, it * BI_TC + cg, a.m, a.k, E);
                     s.Lw = active ? lw : -INFINITY;
                     publish_bound(s.pub, s.tag, s.Lw);
                     warm = true;
@@ -350,26 +365,27 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                 tmem_ld32_issue(tb, ra);
                 tmem_wait_bind(ra);
 #pragma unroll 1
-                for (int c0 = 0; c0 < BI_TC; c0 += 64) {
+                for (int c0 = 0; c0 < CW; c0 += 64) {
                     __syncwarp();
                     tmem_ld32_issue(tb + c0 + 32, rb);
                     {
                         float v[32];
                         as_floats(ra, v);
                         if constexpr (FP8) scale_values(v, f);
-                        sel_chunk(v, active, it * BI_TC + c0, a.m, E, s, mycand, a.cap, heap, r, a.k, a.st);
+                        sel_chunk(v, active, it * BI_TC + cg + c0, a.m, E, s, mycand, a.cap, heap, r, a.k, a.st);
                     }
                     __syncwarp();
                     tmem_wait_bind(rb);
-                    if (c0 + 64 < BI_TC) tmem_ld32_issue(tb + c0 + 64, ra);
+                    if (c0 + 64 < CW) tmem_ld32_issue(tb + c0 + 64, ra);
                     {
                         float v[32];
                         as_floats(rb, v);
                         if constexpr (FP8) scale_values(v, f);
-                        sel_chunk(v, active, it * BI_TC + c0 + 32, a.m, E, s, mycand, a.cap, heap, r, a.k, a.st);
+                        sel_chunk(v, active, it * BI_TC + cg + c0 + 32, a.m, E, s, mycand, a.cap, heap, r, a.k,
+                                  a.st);
                     }
                     __syncwarp();
-                    if (c0 + 64 < BI_TC) tmem_wait_bind(ra);
+                    if (c0 + 64 < CW) tmem_wait_bind(ra);
                 }
                 tc_fence_before();
                 __syncwarp();
@@ -380,7 +396,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             }
             if (active) {
                 atomicMax(&a.lfin_key[u], float_key(fmaxf(s.L, s.Lw)));
-                a.cand_cnt[u * a.nseg + h] = s.cnt;
+                a.cand_cnt[u * a.nseg + g] = s.cnt;
             }
         }
     }
@@ -435,10 +451,11 @@ __device__ __forceinline__ void cursor_next(const CountArgs& a, unsigned total, 
     cursor_unit(a, total, len, c);
 }
 
-// Add a warp's per-item counters of the item tile starting at pos0 to the global counts.
+// Add a warp's per-item counters of the CW columns starting at pos0 to the global counts.
+template <int CW>
 __device__ __forceinline__ void flush_counts(int* cw, int lane, int pos0, int64_t m, int* counts) {
     __syncwarp();
-    for (int c = lane; c < BI_TC; c += 32) {
+    for (int c = lane; c < CW; c += 32) {
         const int x = cw[c];
         if (x != 0) {
             if (pos0 + c < m) atomicAdd(&counts[pos0 + c], x);
@@ -448,8 +465,8 @@ __device__ __forceinline__ void flush_counts(int* cw, int lane, int pos0, int64_
     __syncwarp();
 }
 
-template <bool FP8>
-__global__ void __launch_bounds__(TC_THREADS, 1)
+template <bool FP8, int NG>
+__global__ void __launch_bounds__(tc_threads(NG), 1)
     k_count_tc(const CountArgs a, const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
                const TcLayout L) {
     using Op = Operand<FP8>;
@@ -466,7 +483,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     const int len = a.st->t_end - a.t_begin;
     volatile int* abort = &B->abort;
 
-    setup(B, S, warp);
+    setup(B, S, warp, 2 * NG);
     const uint32_t tmem = B->tmem_base;
 
     if (warp == 0) {
@@ -567,12 +584,15 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             drain_wait(&B->drain, 0u, a.st);
         }
     } else {
+        constexpr int CW = 2 * BI_TC / NG;  // accumulator columns a group reads per tile
         const int ew = warp - 2;
-        const int h = ew >> 2;
+        const int g = ew >> 2;
+        const int h = g & 1;
+        const int cg = (g >> 1) * CW;
         const int q = warp & 3;
         const int r = q * 32 + lane;
-        int* cw = cnt_all + ew * BI_TC;  // this warp's per-item member counters
-        for (int c = lane; c < BI_TC; c += 32) cw[c] = 0;
+        int* cw = cnt_all + ew * CW;  // this warp's per-item member counters (its CW columns)
+        for (int c = lane; c < CW; c += 32) cw[c] = 0;
         __syncwarp();
         // This group consumes global tiles h, h+2, h+4, ... of the CTA's sequence.  `cur` is
         // the current one, `nxt` the one after it, whose per-user record is loaded one tile
@@ -592,7 +612,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         while (cur.valid) {
             if (nxt.valid && nxt.ut * BU + r < a.n) um_nxt = a.meta[nxt.ut * BU + r];
             if (cur.T != curT) {
-                if (curT >= 0) flush_counts(cw, lane, curT * BI_TC, a.m, a.counts);
+                if (curT >= 0) flush_counts<CW>(cw, lane, curT * BI_TC + cg, a.m, a.counts);
                 curT = cur.T;
                 pnh = a.thmax[cur.T];
                 pd = a.tdel[cur.T];
@@ -612,13 +632,13 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                 lo_t = __fsub_rd(um_cur.tau_lo, E);
                 u_orig = um_cur.uorig;
             }
-            const int pos0 = cur.T * BI_TC;
-            const uint32_t tb = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)h * BI_TC;
+            const int pos0 = cur.T * BI_TC + cg;
+            const uint32_t tb = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)h * BI_TC + cg;
             uint32_t ra[32], rb[32];
             tmem_ld32_issue(tb, ra);
             tmem_wait_bind(ra);
 #pragma unroll 1
-            for (int c0 = 0; c0 < BI_TC; c0 += 64) {
+            for (int c0 = 0; c0 < CW; c0 += 64) {
                 __syncwarp();
                 tmem_ld32_issue(tb + c0 + 32, rb);
                 {
@@ -629,7 +649,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                 }
                 __syncwarp();
                 tmem_wait_bind(rb);
-                if (c0 + 64 < BI_TC) tmem_ld32_issue(tb + c0 + 64, ra);
+                if (c0 + 64 < CW) tmem_ld32_issue(tb + c0 + 64, ra);
                 {
                     float v[32];
                     as_floats(rb, v);
@@ -638,7 +658,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                                 a.band_cap, a.st);
                 }
                 __syncwarp();
-                if (c0 + 64 < BI_TC) tmem_wait_bind(ra);
+                if (c0 + 64 < CW) tmem_wait_bind(ra);
             }
             tc_fence_before();
             __syncwarp();
@@ -649,9 +669,120 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             cursor_next(a, total, len, nxt);
             cursor_next(a, total, len, nxt);
         }
-        if (curT >= 0) flush_counts(cw, lane, curT * BI_TC, a.m, a.counts);
+        if (curT >= 0) flush_counts<CW>(cw, lane, curT * BI_TC + cg, a.m, a.counts);
     }
     teardown(B, warp);
+}
+
+// ---------------------------------------------------------------- guard-band check
+
+// One 128-user x 256-item tile per CTA, computed with the operands, TMA boxes, swizzle,
+// descriptors, MMA shape and FP8 descale of the product kernels above, written out with the
+// error bound E of its row instead of being consumed by an epilogue.  128 threads: thread 0
+// loads every K-block at once and issues the MMAs; warp 1 owns the TMEM columns; all four
+// warps read back their 32 accumulator lanes.
+template <bool FP8>
+__global__ void __launch_bounds__(128, 1)
+    k_products_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
+                  const ProductsArgs a) {
+    using Op = Operand<FP8>;
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t* sm = align1024(smem_raw);
+    const int KB = a.dp >> Op::KSHIFT;
+    uint8_t* sA = sm;
+    uint8_t* sB = sm + KB * KB_BYTES_U;
+    __shared__ uint64_t full, done;
+    __shared__ uint32_t tmem_base;
+    __shared__ int abort_flag;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int ut = blockIdx.x, it = blockIdx.y;
+    if (threadIdx.x == 0) {
+        mbar_init(&full, 1);
+        mbar_init(&done, 1);
+        abort_flag = 0;
+        mbar_fence_init();
+    }
+    if (warp == 1) {
+        tmem_alloc(&tmem_base, BI_TC);
+        tmem_relinquish();
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = tmem_base;
+    volatile int* abort = &abort_flag;
+    bool issued = false;
+    if (threadIdx.x == 0) {
+        mbar_expect_tx(&full, KB * (KB_BYTES_U + KB_BYTES_I));
+        for (int kb = 0; kb < KB; ++kb) {
+            tma_load_2d(sA + kb * KB_BYTES_U, &tmA, &full, kb * Op::KELEMS, ut * BU);
+            tma_load_2d(sB + kb * KB_BYTES_I, &tmB, &full, kb * Op::KELEMS, it * BI_TC);
+        }
+        if (mbar_wait(&full, 0u, abort, a.st)) {
+            tc_fence_after();
+            const uint32_t idesc = Op::idesc();
+            for (int kb = 0; kb < KB; ++kb) {
+                const uint64_t ad = sdesc_sw128(smem_u32(sA + kb * KB_BYTES_U));
+                const uint64_t bd = sdesc_sw128(smem_u32(sB + kb * KB_BYTES_I));
+#pragma unroll
+                for (int k = 0; k < 4; ++k) Op::mma(tmem, ad + 2u * k, bd + 2u * k, idesc, (kb | k) != 0 ? 1u : 0u);
+            }
+            tc_commit(&done);
+            issued = true;
+        } else {
+            drain_wait(&full, 0u, a.st);  // the copies must land before the CTA exits
+        }
+    }
+    __syncwarp();
+    if (mbar_wait(&done, 0u, abort, a.st)) {
+        tc_fence_after();
+        const int r = warp * 32 + lane;
+        const int64_t u = (int64_t)ut * BU + r;
+        const bool active = u < a.n;
+        const float thm = a.thmax[it], tdl = a.tdel[it];
+        const float E = active ? err_bound(a.cacc, a.eabs, a.unrm[u], a.unhat[u], a.udel[u], thm, tdl) : 0.f;
+        const float f = (FP8 && active) ? pow2i(fp8_exp(a.uexp[u]) + a.texp[it] - 16) : 1.f;
+        for (int c0 = 0; c0 < BI_TC; c0 += 32) {
+            float v[32];
+            __syncwarp();
+            tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + c0, v);
+            if (!active) continue;
+#pragma unroll
+            for (int j = 0; j < 32; ++j) {
+                const int64_t pos = (int64_t)it * BI_TC + c0 + j;
+                if (pos < a.m) {
+                    const int64_t o = u * a.ldo + a.perm[pos];
+                    a.v[o] = FP8 ? v[j] * f : v[j];
+                    a.E[o] = E;
+                }
+            }
+        }
+    }
+    if (threadIdx.x == 0 && issued) drain_wait(&done, 0u, a.st);  // no MMA in flight at exit
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 1) {
+        tc_fence_after();
+        tmem_dealloc(tmem, BI_TC);
+    }
+}
+
+// ---------------------------------------------------------------- timeout path check
+
+// One warp waits, with the product kernels' bounded wait and a given limit, on an mbarrier
+// whose phase nothing completes (no arrival, no copy): the wait gives up, raises the abort
+// flag and records the timeout in the status word, and the kernel returns normally.  The
+// other lanes then see the abort flag and leave their waits at once.
+__global__ void k_wait_timeout(long long limit, DevStatus* st) {
+    __shared__ uint64_t bar;
+    __shared__ int abort_flag;
+    if (threadIdx.x == 0) {
+        mbar_init(&bar, 1);
+        abort_flag = 0;
+        mbar_fence_init();
+    }
+    __syncthreads();
+    mbar_wait(&bar, 0u, &abort_flag, st, limit);
 }
 
 // Shared-memory plan: two resident buffers when that still leaves two ring slots, else one;
@@ -718,34 +849,103 @@ rkm_status make_tmaps(const void* A, int64_t a_rows, const void* B, int64_t b_ro
     return RKM_OK;
 }
 
-void launch_threshold_tc(const TcInstance* inst, int count, long long total_units, int kheap, int max_dp,
-                         bool fp8, int num_sms, cudaStream_t s) {
+namespace {
+
+TcLayout threshold_layout(int ng, int kheap, int max_dp, bool fp8) {
     const int KB = fp8 ? max_dp / 128 : max_dp / 64;
-    const TcLayout L = make_layout(KB * KB_BYTES_U, KB_BYTES_I, 2u * BU * kheap * 4u + 2u * BU * 8u, MAX_SLOTS);
+    return make_layout(KB * KB_BYTES_U, KB_BYTES_I, (uint32_t)ng * BU * kheap * 4u + (uint32_t)ng * BU * 8u,
+                       MAX_SLOTS);
+}
+
+template <bool FP8, int NG>
+void launch_threshold_ng(const TcInstance* inst, int count, long long total_units, int kheap, const TcLayout& L,
+                         int grid, cudaStream_t s) {
+    cudaFuncSetAttribute(k_threshold_tc<FP8, NG>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.bytes);
+    k_threshold_tc<FP8, NG><<<grid, tc_threads(NG), L.bytes, s>>>(inst, count, total_units, kheap, L);
+}
+
+}  // namespace
+
+// Two groups unless four are asked for: measured on GB300 (BF16, d = 64 and 128), four
+// groups made the threshold pass 1.5-1.8x slower.  Each group's heap then sees a quarter of
+// the items, so its bound is lower and it records more candidates (exact rescoring took 2.4x
+// longer), and 18 warps leave 96 registers per thread, so the hit path spills.
+int threshold_groups(int kheap, int max_dp, bool fp8, int want) {
+    if (want != 4 || kheap > 32) return 2;
+    return threshold_layout(4, kheap, max_dp, fp8).slots >= 2 ? 4 : 2;
+}
+
+// Four groups when the product of a tile is one K-block deep (BF16 d <= 64, FP8 d <= 128):
+// the MMA of a tile is then shortest and eight warps reading each tile kept the counting
+// pass 15 % faster at d = 64 on GB300; at two K-blocks and more the two were equal.
+int count_groups(int dp, bool fp8, int want) {
+    if (want == 2 || want == 4) return want;
+    return (fp8 ? dp <= 128 : dp <= 64) ? 4 : 2;
+}
+
+void launch_threshold_tc(const TcInstance* inst, int count, long long total_units, int kheap, int max_dp,
+                         bool fp8, int ng, int num_sms, cudaStream_t s) {
+    if (ng != 4) ng = 2;
+    const TcLayout L = threshold_layout(ng, kheap, max_dp, fp8);
     const int grid = (int)(total_units < num_sms ? total_units : num_sms);
     if (grid < 1) return;
     note_launch();
     if (fp8) {
-        cudaFuncSetAttribute(k_threshold_tc<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.bytes);
-        k_threshold_tc<true><<<grid, TC_THREADS, L.bytes, s>>>(inst, count, total_units, kheap, L);
+        if (ng == 4) launch_threshold_ng<true, 4>(inst, count, total_units, kheap, L, grid, s);
+        else launch_threshold_ng<true, 2>(inst, count, total_units, kheap, L, grid, s);
     } else {
-        cudaFuncSetAttribute(k_threshold_tc<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.bytes);
-        k_threshold_tc<false><<<grid, TC_THREADS, L.bytes, s>>>(inst, count, total_units, kheap, L);
+        if (ng == 4) launch_threshold_ng<false, 4>(inst, count, total_units, kheap, L, grid, s);
+        else launch_threshold_ng<false, 2>(inst, count, total_units, kheap, L, grid, s);
     }
 }
 
-void launch_count_tc(const CountArgs& a, const void* tmapA, const void* tmapB, bool fp8, cudaStream_t s) {
+void launch_wait_timeout(long long limit, DevStatus* st, cudaStream_t s) {
+    note_launch();
+    k_wait_timeout<<<1, 32, 0, s>>>(limit, st);
+}
+
+void launch_products_tc(const ProductsArgs& a, const void* tmapA, const void* tmapB, bool fp8, cudaStream_t s) {
     const int KB = fp8 ? a.dp / 128 : a.dp / 64;
-    const TcLayout L = make_layout(KB * KB_BYTES_I, KB_BYTES_U, 8u * BI_TC * 4u, MAX_SLOTS);
+    // At least 120 KB of shared memory, so one CTA per SM: no CTA waits for TMEM columns.
+    uint32_t bytes = 1024u + (uint32_t)KB * (KB_BYTES_U + KB_BYTES_I);
+    if (bytes < 120u * 1024u) bytes = 120u * 1024u;
+    const dim3 grid((unsigned)((a.n + BU - 1) / BU), (unsigned)((a.m + BI_TC - 1) / BI_TC));
+    if (grid.x == 0 || grid.y == 0) return;
     const CUtensorMap& mA = *static_cast<const CUtensorMap*>(tmapA);
     const CUtensorMap& mB = *static_cast<const CUtensorMap*>(tmapB);
     note_launch();
     if (fp8) {
-        cudaFuncSetAttribute(k_count_tc<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.bytes);
-        k_count_tc<true><<<a.num_sms, TC_THREADS, L.bytes, s>>>(a, mA, mB, L);
+        cudaFuncSetAttribute(k_products_tc<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+        k_products_tc<true><<<grid, 128, bytes, s>>>(mA, mB, a);
     } else {
-        cudaFuncSetAttribute(k_count_tc<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.bytes);
-        k_count_tc<false><<<a.num_sms, TC_THREADS, L.bytes, s>>>(a, mA, mB, L);
+        cudaFuncSetAttribute(k_products_tc<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+        k_products_tc<false><<<grid, 128, bytes, s>>>(mA, mB, a);
+    }
+}
+
+namespace {
+
+template <bool FP8, int NG>
+void launch_count_ng(const CountArgs& a, const CUtensorMap& mA, const CUtensorMap& mB, cudaStream_t s) {
+    const int KB = FP8 ? a.dp / 128 : a.dp / 64;
+    // per-warp member counters: 4 NG warps x (512 / NG) columns
+    const TcLayout L = make_layout(KB * KB_BYTES_I, KB_BYTES_U, 4u * NG * (2u * BI_TC / NG) * 4u, MAX_SLOTS);
+    cudaFuncSetAttribute(k_count_tc<FP8, NG>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.bytes);
+    k_count_tc<FP8, NG><<<a.num_sms, tc_threads(NG), L.bytes, s>>>(a, mA, mB, L);
+}
+
+}  // namespace
+
+void launch_count_tc(const CountArgs& a, const void* tmapA, const void* tmapB, bool fp8, cudaStream_t s) {
+    const CUtensorMap& mA = *static_cast<const CUtensorMap*>(tmapA);
+    const CUtensorMap& mB = *static_cast<const CUtensorMap*>(tmapB);
+    note_launch();
+    if (fp8) {
+        if (a.groups == 4) launch_count_ng<true, 4>(a, mA, mB, s);
+        else launch_count_ng<true, 2>(a, mA, mB, s);
+    } else {
+        if (a.groups == 4) launch_count_ng<false, 4>(a, mA, mB, s);
+        else launch_count_ng<false, 2>(a, mA, mB, s);
     }
 }
 

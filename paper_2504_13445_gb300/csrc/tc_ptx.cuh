@@ -50,12 +50,14 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
 
 // Wait until the phase with the given parity has completed.  Returns false on timeout
 // (and raises `abort` and st->timeout) or when `abort` was raised by another thread.
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, volatile int* abort, DevStatus* st) {
+// `limit` is in SM clocks (the product kernels use the default).
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, volatile int* abort, DevStatus* st,
+                                          long long limit = RKM_WAIT_CYCLES) {
     if (mbar_try_wait(bar, parity)) return true;
     const long long t0 = clock64();
     while (!mbar_try_wait(bar, parity)) {
         if (*abort) return false;
-        if (clock64() - t0 > RKM_WAIT_CYCLES) {
+        if (clock64() - t0 > limit) {
             *abort = 1;
             st->timeout = 1u;
             return false;

@@ -123,3 +123,30 @@ def test_serving_rejections(rkm, resident):
         with rkm.Server(ctx, slots=1, max_batch_items=4096, memory_bytes=300_000) as srv:
             with pytest.raises(rkm.RkmError, match="arena"):
                 srv.submit(np.zeros((4000, W.d), dtype=np.float32))
+
+
+def test_state_save_and_load_round_trip(rkm, resident, tmp_path):
+    """A saved serving state restores the resident set in a fresh context (no threshold
+    pass): every request's counts equal the oracle's; a corrupted file is refused with
+    RKM_EIO and leaves the loaded state in place."""
+    W, tau, tid, arrivals, reqs, expect = resident
+    path = str(tmp_path / "resident.rkmstate")
+    with rkm.Context("bf16") as ctx:
+        with pytest.raises(rkm.RkmError):
+            ctx.state_save(path)  # no resident set yet
+        ctx.resident_set(torch.from_numpy(W.U).cuda(), torch.from_numpy(tau).cuda(),
+                         torch.from_numpy(tid.astype(np.int32)).cuda())
+        ctx.state_save(path)
+    with rkm.Context("bf16") as fresh:
+        fresh.state_load(path)
+        for Q, e in zip(reqs[:12], expect[:12]):
+            np.testing.assert_array_equal(fresh.query_new_items(torch.from_numpy(Q).cuda()).cpu().numpy(), e)
+        blob = bytearray(open(path, "rb").read())
+        blob[100] ^= 1
+        bad = str(tmp_path / "corrupt.rkmstate")
+        open(bad, "wb").write(bytes(blob))
+        with pytest.raises(rkm.RkmError) as err:
+            fresh.state_load(bad)
+        assert err.value.status == 9  # RKM_EIO
+        Q, e = reqs[0], expect[0]
+        np.testing.assert_array_equal(fresh.query_new_items(torch.from_numpy(Q).cuda()).cpu().numpy(), e)

@@ -46,3 +46,35 @@ def test_noalloc_rejects_n_beyond_the_scratch(rkm):
     scores = torch.zeros(10_000, dtype=torch.int32, device="cuda")
     with pytest.raises(rkm.RkmError, match="4096"):
         rkm.rkm_topn_scores_noalloc(scores, 5000)
+
+
+def _check_against_oracle(rkm, scores_np, N):
+    scores = torch.from_numpy(scores_np.astype(np.int32)).cuda()
+    ids, sc = rkm.rkm_topn_scores_noalloc(scores, N)
+    torch.cuda.synchronize()
+    ids_o, sc_o = oracle.topn(scores_np.astype(np.int64), N)
+    np.testing.assert_array_equal(ids.cpu().numpy(), ids_o)
+    np.testing.assert_array_equal(sc.cpu().numpy(), sc_o)
+
+
+def test_noalloc_capacity_edge_and_ties(rkm):
+    """N at the scratch capacity (4096) and N = m, on arrays whose many equal scores straddle
+    the N-th key; then N = 4096 followed by N = 7, so that keys left in the shared array by a
+    larger call are never read by a smaller one."""
+    rng = np.random.default_rng(5)
+    tied = rng.integers(0, 6, size=9_000)           # ~1500 items per score value
+    _check_against_oracle(rkm, tied, 4096)
+    small = rng.integers(0, 3, size=4096)
+    _check_against_oracle(rkm, small, 4096)         # N = m at the capacity
+    _check_against_oracle(rkm, small[:777], 777)    # N = m below it
+    _check_against_oracle(rkm, tied, 4096)
+    _check_against_oracle(rkm, tied, 7)
+
+
+def test_noalloc_signed_scores(rkm):
+    """Signed int32 scores (negative values, INT32_MIN and INT32_MAX) order as integers."""
+    rng = np.random.default_rng(6)
+    s = rng.integers(-50, 50, size=5_000)
+    s[[3, 10, 4000]] = [np.iinfo(np.int32).min, np.iinfo(np.int32).max, -1]
+    for N in (1, 33, 4096):
+        _check_against_oracle(rkm, s, N)
