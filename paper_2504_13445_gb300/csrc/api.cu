@@ -126,6 +126,13 @@ struct rkm_ctx {
     TcInstance* batch_host = nullptr;
     int batch_host_cap = 0;
     Buf batch_dev;
+    // Batches: per-problem descriptors of the launches after the threshold pass (pinned host
+    // staging, stable while a captured graph replays them, and device copies): the jobs and
+    // the counting descriptors of both stages.
+    BatchJob* jobs_host = nullptr;
+    CountInstance* bcount_host = nullptr;
+    int jobs_cap = 0;
+    Buf jobs_dev, bcount_dev;
     std::string tune_cache;
     std::map<std::string, std::pair<int, int64_t>> tune;  // size bucket -> (group, first-stage items)
     bool tune_loaded = false;
@@ -157,6 +164,11 @@ struct rkm_ctx {
         ev_pool.pop_back();
         return e;
     }
+
+    // Descriptors of the tensor-core counting launches of a call (slot 0: the first stage or
+    // the only one, slot 1: the second stage): pinned host staging and device copies.
+    CountInstance* cinst_host = nullptr;
+    Buf cinst_dev;
 
     // Descriptors of the tensor-core threshold launch: pinned host staging and device copy.
     TcInstance* inst_host = nullptr;
@@ -222,6 +234,10 @@ struct rkm_ctx {
         ev_pool.clear();
         if (inst_dev.p) cudaFree(inst_dev.p);
         inst_dev = Buf{};
+        if (cinst_dev.p) cudaFree(cinst_dev.p);
+        cinst_dev = Buf{};
+        if (cinst_host) cudaFreeHost(cinst_host);
+        cinst_host = nullptr;
         if (inst_host) cudaFreeHost(inst_host);
         inst_host = nullptr;
         inst_host_cap = 0;
@@ -239,6 +255,15 @@ struct rkm_ctx {
         if (batch_host) cudaFreeHost(batch_host);
         batch_host = nullptr;
         batch_host_cap = 0;
+        if (jobs_host) cudaFreeHost(jobs_host);
+        if (bcount_host) cudaFreeHost(bcount_host);
+        jobs_host = nullptr;
+        bcount_host = nullptr;
+        jobs_cap = 0;
+        if (jobs_dev.p) cudaFree(jobs_dev.p);
+        if (bcount_dev.p) cudaFree(bcount_dev.p);
+        jobs_dev = Buf{};
+        bcount_dev = Buf{};
     }
 };
 
@@ -702,10 +727,26 @@ rkm_status order_users(rkm_ctx* c, const PathShape& ps, const float* U, int64_t 
     return RKM_OK;
 }
 
+// Arguments and TMA maps of a tensor-core counting launch over one problem (unit_begin is
+// written on the device).
+rkm_status count_descriptor(const PathShape& ps, int64_t n, const UserOrder& uo, const ItemSide& it,
+                            const CountArgs& a, CountInstance* out) {
+    TmapPair tm;
+    const int64_t n_pad = round_up(std::max<int64_t>(n, 1), BU);
+    TRY(make_tmaps(uo.pack, n_pad, it.pack, it.m_pad, ps.dp, BI_TC, ps.elem_bytes, &tm));
+    out->tmA = tm.a;
+    out->tmB = tm.b;
+    out->a = a;
+    out->unit_begin = 0;
+    return RKM_OK;
+}
+
 // One counting stage over item tiles [t_begin, t_end) (t_end from the device if t_end_dev).
+// slot: descriptor slot of the tensor-core launch (0 or 1; distinct for the two stages of
+// one call, whose descriptors are copied before either runs).
 rkm_status count_stage(rkm_ctx* c, const PathShape& ps, int64_t n, const UserOrder& uo, const ItemSide& it,
                        bool new_items, int t_begin, int t_end, bool t_end_from_dev, const ExactData& x,
-                       const double* tau, const int* tid, int* cnt, int2* band, cudaStream_t s) {
+                       const double* tau, const int* tid, int* cnt, int2* band, cudaStream_t s, int slot = 0) {
     int* nprefix;
     unsigned* unit_off;
     TRY(c->ensure(c->nprefix, std::max<int64_t>(it.tiles, 1), &nprefix));
@@ -740,10 +781,19 @@ rkm_status count_stage(rkm_ctx* c, const PathShape& ps, int64_t n, const UserOrd
     a.st = c->st;
     a.num_sms = c->num_sms;
     if (ps.tc) {
-        TmapPair tm;
-        const int64_t n_pad = round_up(std::max<int64_t>(n, 1), BU);
-        TRY(make_tmaps(uo.pack, n_pad, it.pack, it.m_pad, ps.dp, BI_TC, ps.elem_bytes, &tm));
-        launch_count_tc(a, &tm.a, &tm.b, ps.fp8, s);
+        if (!c->cinst_host) {
+            if (cudaMallocHost(&c->cinst_host, 2 * sizeof(CountInstance)) != cudaSuccess) {
+                cudaGetLastError();
+                c->cinst_host = nullptr;
+                return fail(RKM_ENOMEM, "pinned counting descriptors");
+            }
+        }
+        CountInstance* dev;
+        TRY(c->ensure(c->cinst_dev, 2, &dev));
+        TRY(count_descriptor(ps, n, uo, it, a, &c->cinst_host[slot]));
+        CUDA_TRY(cudaMemcpyAsync(dev + slot, c->cinst_host + slot, sizeof(CountInstance), cudaMemcpyHostToDevice, s));
+        launch_count_prefix(dev + slot, 1, &c->st->launch_units, s);
+        launch_count_tc(dev + slot, 1, &c->st->launch_units, ps.dp, ps.fp8, a.groups, c->num_sms, s);
     } else {
         launch_count_simt(a, s);
     }
@@ -1018,7 +1068,7 @@ rkm_status count_enqueue(rkm_ctx* c, const PathShape& ps, int64_t n, const ItemS
             launch_topn(cnt, it.perm, m0, nullptr, N, tids_c0, tsc_c0, c->st, s);
             launch_filter_cut(tsc_c0, N, it.tmax, uo.ucum, it.tiles, t0, ps.item_tile, it.m, c->st, s);
         }
-        TRY(count_stage(c, ps, n, uo, it, false, t0, 0, true, x, tau, tid, cnt, band, s));
+        TRY(count_stage(c, ps, n, uo, it, false, t0, 0, true, x, tau, tid, cnt, band, s, 1));
         TRY(band_stage(c, it, false, x, tau, tid, cnt, band, s));
         Phase ph(c, s, RKM_PHASE_TOPN);
         launch_topn(cnt, it.perm, it.m, &c->st->m_counted, N, ids, top_scores, c->st, s);
@@ -1464,9 +1514,146 @@ int64_t instance_cost(const rkm_instance& I, const PathShape& ps) {
     return ((I.n + BU - 1) / BU) * ((I.m + BI_TC - 1) / BI_TC) * (ps.dp / 64);
 }
 
+// Pinned staging and device arrays of a batch's job and counting descriptors.
+rkm_status batch_job_arrays(rkm_ctx* c, int count, BatchJob** jd, CountInstance** cd) {
+    if (c->jobs_cap < count) {
+        if (c->jobs_host) cudaFreeHost(c->jobs_host);
+        if (c->bcount_host) cudaFreeHost(c->bcount_host);
+        c->jobs_host = nullptr;
+        c->bcount_host = nullptr;
+        c->jobs_cap = 0;
+        if (cudaMallocHost(&c->jobs_host, (size_t)count * sizeof(BatchJob)) != cudaSuccess ||
+            cudaMallocHost(&c->bcount_host, 2 * (size_t)count * sizeof(CountInstance)) != cudaSuccess) {
+            cudaGetLastError();
+            return fail(RKM_ENOMEM, "pinned batch descriptors for %d instances", count);
+        }
+        c->jobs_cap = count;
+    }
+    TRY(c->ensure(c->jobs_dev, count, jd));
+    TRY(c->ensure(c->bcount_dev, 2 * (int64_t)count, cd));
+    return RKM_OK;
+}
+
+// The steps after the threshold launch of a tensor-core batch, as launches over all
+// instances: exact thresholds (one launch); per instance the K4 user order (it needs that
+// instance's thresholds); then one launch each for clearing the counts, the first-stage unit
+// lists, the first counting stage (persistent, over every instance's units), band rescoring,
+// the first-stage top-N, the filter cut, the second-stage unit lists, the second counting
+// stage, band rescoring and the final top-N.
+rkm_status batch_enqueue_tc(rkm_ctx* c, const rkm_instance* inst, int count, std::vector<InstWork>& w,
+                            int max_dp, cudaStream_t s) {
+    BatchJob* jd;
+    CountInstance* cd;
+    TRY(batch_job_arrays(c, count, &jd, &cd));
+    BatchJob* J = c->jobs_host;
+    int64_t users = 0, max_m = 1;
+    for (int i = 0; i < count; ++i) {
+        rkm_ctx* sc = c->sub[i];
+        const rkm_instance& I = inst[i];
+        const InstWork& x = w[i];
+        BatchJob& j = J[i];
+        j = BatchJob{};
+        j.x = ExactData{I.U, I.ldu, x.up.e, x.up.q, I.P, I.ldp, x.it.rp.e, x.it.rp.q, I.d, (int)round_up(I.d, 8),
+                        &sc->st->off_grid};
+        j.cand = x.pl.cand;
+        j.cand_cnt = x.pl.cand_cnt;
+        j.lfin = x.pl.lfin;
+        j.cap = x.pl.cap;
+        j.nseg = x.pl.nseg;
+        j.item_perm = x.it.perm;
+        j.n = I.n;
+        j.m = I.m;
+        j.k = I.k;
+        j.N = I.N;
+        j.keys = x.pl.keys;
+        j.kid = x.pl.kid;
+        j.tau = x.tau;
+        j.tid = x.tid;
+        j.user_begin = users;
+        j.st = sc->st;
+        users += I.n;
+        max_m = std::max<int64_t>(max_m, I.m);
+    }
+    // The exact thresholds read only the fields set so far; the later copy of the completed
+    // jobs only adds fields, so either copy may read the staging at any time.
+    CUDA_TRY(cudaMemcpyAsync(jd, J, (size_t)count * sizeof(BatchJob), cudaMemcpyHostToDevice, s));
+    launch_exact_tau_multi(jd, count, users, s);
+    const bool fp8 = w[0].ps.fp8;
+    const int groups = count_groups(max_dp, fp8, c->opts.epilogue_groups);
+    for (int i = 0; i < count; ++i) {
+        rkm_ctx* sc = c->sub[i];
+        const rkm_instance& I = inst[i];
+        InstWork& x = w[i];
+        BatchJob& j = J[i];
+        TRY(count_prepare(sc, x.ps, I.U, I.n, I.ldu, I.P, I.ldp, I.d, x.up, x.it, x.tau, x.tid, &x.cp, s));
+        int2* band;
+        TRY(ensure_band(sc, &band));
+        TRY(sc->ensure(sc->nprefix, std::max<int64_t>(x.it.tiles, 1), &j.nprefix));
+        TRY(sc->ensure(sc->unit_off, x.it.tiles + 2, &j.unit_off));
+        TRY(sc->ensure(sc->top_ids, I.N, &j.top_ids_c0));
+        TRY(sc->ensure(sc->top_sc, I.N, &j.top_sc_c0));
+        const int tiles = (int)x.it.tiles;
+        const int64_t c0 = std::max<int64_t>(4 * (int64_t)I.N, sc->stage1_items);
+        j.tmax = x.it.tmax;
+        j.ucum = x.cp.uo.ucum;
+        j.tiles = tiles;
+        j.t0 = c->opts.filter ? (int)std::min<int64_t>(tiles, (c0 + x.ps.item_tile - 1) / x.ps.item_tile) : tiles;
+        j.tile_items = x.ps.item_tile;
+        j.group = sc->count_group;
+        j.counts = x.cp.cnt;
+        j.band = band;
+        j.band_cap = (unsigned)sc->band_cap;
+        j.ids = I.ids;
+        j.top_scores = I.top_scores;
+        CountArgs a{};
+        a.A = x.cp.uo.pack;
+        a.B = x.it.pack;
+        a.n = I.n;
+        a.m = x.it.m;
+        a.dp = x.ps.dp;
+        a.meta = x.cp.uo.meta;
+        a.item_id = x.it.perm;
+        a.new_items = false;
+        a.tmax = x.it.tmax;
+        a.thmax = x.it.thmax;
+        a.tdel = x.it.tdel;
+        a.texp = x.it.texp;
+        a.nprefix = j.nprefix;
+        a.unit_off = j.unit_off;
+        a.group = j.group;
+        a.groups = groups;
+        a.cacc = x.ps.cacc;
+        a.eabs = x.ps.eabs;
+        a.counts = j.counts;
+        a.band = band;
+        a.band_cap = j.band_cap;
+        a.st = sc->st;
+        a.num_sms = c->num_sms;
+        for (int stage = 0; stage < 2; ++stage) {
+            a.t_begin = stage == 0 ? 0 : j.t0;
+            TRY(count_descriptor(x.ps, I.n, x.cp.uo, x.it, a, &c->bcount_host[stage * count + i]));
+        }
+    }
+    CUDA_TRY(cudaMemcpyAsync(jd, J, (size_t)count * sizeof(BatchJob), cudaMemcpyHostToDevice, s));
+    CUDA_TRY(cudaMemcpyAsync(cd, c->bcount_host, 2 * (size_t)count * sizeof(CountInstance), cudaMemcpyHostToDevice,
+                             s));
+    launch_batch_reset(jd, count, max_m, s);
+    for (int stage = 1; stage <= 2; ++stage) {
+        CountInstance* ci = cd + (stage - 1) * count;
+        launch_build_units_multi(jd, count, stage, s);
+        launch_count_prefix(ci, count, &c->st->launch_units, s);
+        launch_count_tc(ci, count, &c->st->launch_units, max_dp, fp8, groups, c->num_sms, s);
+        launch_band_multi(jd, count, s);
+        launch_topn_multi(jd, count, stage, s);
+        if (stage == 1) launch_filter_cut_multi(jd, count, s);
+    }
+    return RKM_OK;
+}
+
 // Every kernel of a batch, in order, on one stream, without host waits (so that the sequence
 // can be captured into a graph): per instance prep and threshold arguments; one threshold
-// launch over all instances (largest first); per instance exact rescoring, counting, top-N.
+// launch over all instances (largest first); then the remaining steps (one launch over all
+// instances each on the tensor-core paths, per instance on the FP32 path).
 rkm_status batch_enqueue(rkm_ctx* c, const rkm_instance* inst, int count, cudaStream_t s) {
     std::vector<InstWork> w(count);
     // Every instance of the persistent threshold launch has one candidate segment per
@@ -1516,6 +1703,7 @@ rkm_status batch_enqueue(rkm_ctx* c, const rkm_instance* inst, int count, cudaSt
         }
         CUDA_TRY(cudaMemcpyAsync(dev, c->batch_host, (size_t)count * sizeof(TcInstance), cudaMemcpyHostToDevice, s));
         launch_threshold_tc(dev, count, units, kheap, max_dp, w[0].ps.fp8, nseg, c->num_sms, s);
+        return batch_enqueue_tc(c, inst, count, w, max_dp, s);
     } else {
         for (int i = 0; i < count; ++i) launch_threshold_simt(w[i].pl.a, s);
     }
@@ -1692,11 +1880,14 @@ extern "C" rkm_status rkm_topn_batch(rkm_ctx* c, const rkm_instance* inst, int c
     CUDA_TRY(cudaGetLastError());
     unsigned long long launches = replay ? c->graph_kernels : g_launches.load() - l0;
     // Instances that overflowed a buffer (or failed a check) inside the batch are recomputed by
-    // the retrying single-instance path; their workspace may grow, so the graph is rebuilt.
-    bool redo = false;
+    // the retrying single-instance path; their workspace may grow, so the graph is rebuilt.  A
+    // wait that gave up stops a launch shared by every instance (it is recorded in one
+    // instance's status), so then every instance is recomputed.
+    bool redo = false, any_timeout = false;
+    for (int i = 0; i < count; ++i) any_timeout = any_timeout || c->sub[i]->st_host->timeout != 0u;
     for (int i = 0; i < count; ++i) {
         const DevStatus& st = *c->sub[i]->st_host;
-        if (st.cand_overflow || st.band_overflow || st.internal_error || st.timeout) {
+        if (st.cand_overflow || st.band_overflow || st.internal_error || any_timeout) {
             const rkm_instance& I = inst[i];
             const unsigned long long l1 = g_launches.load();
             TRY(rkm_topn(c->sub[i], I.U, I.n, I.ldu, I.P, I.m, I.ldp, I.d, I.k, I.N, I.ids, I.top_scores, nullptr,

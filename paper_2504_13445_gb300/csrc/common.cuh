@@ -35,7 +35,8 @@ struct DevStatus {
     int m_counted;                // items whose scores are complete (rkm_topn)
     unsigned long long cand_total;      // candidates kept for exact rescoring
     unsigned long long pairs_evaluated; // products computed by the counting pass
-    unsigned long long pad[4];
+    unsigned long long launch_units;    // work units of the current tensor-core counting launch
+    unsigned long long pad[3];
 };
 
 // Per-user data of the counting pass, one 32-byte record per user in ratio order:

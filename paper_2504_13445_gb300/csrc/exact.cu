@@ -61,6 +61,118 @@ __device__ __forceinline__ float key_to_float(unsigned k) {
     return __uint_as_float(b);
 }
 
+// Number of keys[0 .. cnt) >= K, summed over the warp.
+__device__ __forceinline__ int count_at_least(const unsigned long long* keys, int cnt, unsigned long long K, int lane) {
+    int c = 0;
+    for (int j = lane; j < cnt; j += 32) c += keys[j] >= K;
+    return warp_sum(c);
+}
+
+// Moves the candidates whose exact key is at least the k-th largest key K to the front of
+// keys/ids and returns how many there are (k, plus any ties with K).  K is built one bit at a
+// time from the top: a bit is kept when at least k keys reach the prefix with it set.  The
+// full ranking then runs over about k candidates instead of all of them (a wide guard band,
+// as on the FP8 path, keeps hundreds per user).  All 32 lanes call it.
+__device__ __forceinline__ int keep_top_keys(unsigned long long* keys, int* ids, int cnt, int k, int lane) {
+    unsigned long long K = 0ull;
+    for (int b = 63; b >= 0; --b) {
+        const unsigned long long t = K | (1ull << b);
+        if (count_at_least(keys, cnt, t, lane) >= k) K = t;
+    }
+    const unsigned lt_mask = (1u << lane) - 1u;
+    int out = 0;
+    for (int base = 0; base < cnt; base += 32) {
+        const int j = base + lane;
+        const unsigned long long key = j < cnt ? keys[j] : 0ull;
+        const int id = j < cnt ? ids[j] : 0;
+        const bool take = j < cnt && key >= K;
+        const unsigned mask = __ballot_sync(0xffffffffu, take);
+        // Every lane has read its entry (the ballot orders it before the writes), and writes
+        // go to slots at or before the ones read in this round.
+        if (take) {
+            const int slot = out + __popc(mask & lt_mask);
+            keys[slot] = key;
+            ids[slot] = id;
+        }
+        out += __popc(mask);
+        __syncwarp();
+    }
+    return out;
+}
+
+// Exact tau_u, t_u (and S_k(u) when topk != null) of user u from its candidate lists; one
+// warp per user, all 32 lanes call it.  Returns the number of candidates kept.
+__device__ __forceinline__ int exact_user(const ExactData& x, bool grid, const Cand* __restrict__ cand,
+                                          const int* __restrict__ cand_cnt, const unsigned* __restrict__ lfin_key,
+                                          int cap, int nseg, const int* __restrict__ item_perm, int k,
+                                          unsigned long long* __restrict__ keys, int* __restrict__ kid,
+                                          double* __restrict__ tau, int* __restrict__ tid, int* __restrict__ topk,
+                                          DevStatus* st, int64_t u, int lane) {
+    const unsigned lt_mask = (1u << lane) - 1u;
+    const float L = key_to_float(lfin_key[u]);
+    unsigned long long* kk = keys + u * (int64_t)nseg * cap;
+    int* ki = kid + u * (int64_t)nseg * cap;
+    int kept = 0;
+    for (int h = 0; h < nseg; ++h) {
+        const int cnt = cand_cnt[u * nseg + h];
+        const Cand* c = cand + (u * nseg + h) * (int64_t)cap;
+        for (int base = 0; base < cnt; base += 32) {
+            const int j = base + lane;
+            bool keep = false;
+            Cand cj;
+            cj.ub = 0.f;
+            cj.pos = 0;
+            if (j < cnt) {
+                cj = c[j];
+                keep = cj.ub >= L;
+            }
+            const unsigned mask = __ballot_sync(0xffffffffu, keep);
+            if (keep) {
+                const int slot = kept + __popc(mask & lt_mask);
+                const int io = item_perm[cj.pos];
+                kk[slot] = double_key(exact_dot(x, grid, u, io));
+                ki[slot] = io;
+            }
+            kept += __popc(mask);
+        }
+    }
+    __syncwarp();
+    if (kept < k) {
+        if (lane == 0) st->internal_error = 1u;
+        return kept;
+    }
+    const int kept_all = kept;
+    if (kept > 2 * 32) kept = keep_top_keys(kk, ki, kept, k, lane);
+    // Rank of each kept candidate under (score desc, id asc) = the number of candidates
+    // before it.  Candidates are visited 32 at a time and broadcast by shuffles.
+    for (int j0 = 0; j0 < kept; j0 += 32) {
+        const int j = j0 + lane;
+        const bool mine = j < kept;
+        const unsigned long long key = mine ? kk[j] : 0ull;
+        const int id = mine ? ki[j] : 0x7fffffff;
+        int rank = 0;
+        for (int r0 = 0; r0 < kept; r0 += 32) {
+            const int rn = (kept - r0 < 32) ? kept - r0 : 32;
+            const unsigned long long k2l = (r0 + lane < kept) ? kk[r0 + lane] : 0ull;
+            const int i2l = (r0 + lane < kept) ? ki[r0 + lane] : 0x7fffffff;
+            for (int r = 0; r < rn; ++r) {
+                const unsigned long long k2 = __shfl_sync(0xffffffffu, k2l, r);
+                const int i2 = __shfl_sync(0xffffffffu, i2l, r);
+                rank += (k2 > key) || (k2 == key && i2 < id);
+            }
+        }
+        if (mine && rank < k) {
+            if (topk) topk[u * (int64_t)k + rank] = id;
+            if (rank == k - 1) {
+                tau[u] = key_to_double(key);
+                tid[u] = id;
+            }
+        }
+    }
+    __syncwarp();
+    return kept_all;
+}
+
 // Latency-bound (dependent loads of each user's candidates, ids and codes): six blocks per
 // SM (40 registers, a few spilled) hide more of it than the four that 63 registers allow.
 __global__ void __launch_bounds__(256, 6) k_exact_tau(ExactData x, const Cand* __restrict__ cand, const int* __restrict__ cand_cnt,
@@ -70,85 +182,54 @@ __global__ void __launch_bounds__(256, 6) k_exact_tau(ExactData x, const Cand* _
                             int* __restrict__ kid, double* __restrict__ tau, int* __restrict__ tid,
                             int* __restrict__ topk, DevStatus* st) {
     const int lane = threadIdx.x & 31;
-    const unsigned lt_mask = (1u << lane) - 1u;
     const bool grid = *x.off_grid == 0u;
     const int64_t warps = ((int64_t)gridDim.x * blockDim.x) >> 5;
     unsigned long long kept_total = 0;
-    for (int64_t u = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; u < n; u += warps) {
-        const float L = key_to_float(lfin_key[u]);
-        unsigned long long* kk = keys + u * (int64_t)nseg * cap;
-        int* ki = kid + u * (int64_t)nseg * cap;
-        int kept = 0;
-        for (int h = 0; h < nseg; ++h) {
-            const int cnt = cand_cnt[u * nseg + h];
-            const Cand* c = cand + (u * nseg + h) * (int64_t)cap;
-            for (int base = 0; base < cnt; base += 32) {
-                const int j = base + lane;
-                bool keep = false;
-                Cand cj;
-                cj.ub = 0.f;
-                cj.pos = 0;
-                if (j < cnt) {
-                    cj = c[j];
-                    keep = cj.ub >= L;
-                }
-                const unsigned mask = __ballot_sync(0xffffffffu, keep);
-                if (keep) {
-                    const int slot = kept + __popc(mask & lt_mask);
-                    const int io = item_perm[cj.pos];
-                    kk[slot] = double_key(exact_dot(x, grid, u, io));
-                    ki[slot] = io;
-                }
-                kept += __popc(mask);
-            }
-        }
-        __syncwarp();
-        if (lane == 0) kept_total += (unsigned long long)kept;
-        if (kept < k) {
-            if (lane == 0) st->internal_error = 1u;
-            continue;
-        }
-        // Rank of each kept candidate under (score desc, id asc) = the number of candidates
-        // before it.  Candidates are visited 32 at a time and broadcast by shuffles.
-        for (int j0 = 0; j0 < kept; j0 += 32) {
-            const int j = j0 + lane;
-            const bool mine = j < kept;
-            const unsigned long long key = mine ? kk[j] : 0ull;
-            const int id = mine ? ki[j] : 0x7fffffff;
-            int rank = 0;
-            for (int r0 = 0; r0 < kept; r0 += 32) {
-                const int rn = (kept - r0 < 32) ? kept - r0 : 32;
-                const unsigned long long k2l = (r0 + lane < kept) ? kk[r0 + lane] : 0ull;
-                const int i2l = (r0 + lane < kept) ? ki[r0 + lane] : 0x7fffffff;
-                for (int r = 0; r < rn; ++r) {
-                    const unsigned long long k2 = __shfl_sync(0xffffffffu, k2l, r);
-                    const int i2 = __shfl_sync(0xffffffffu, i2l, r);
-                    rank += (k2 > key) || (k2 == key && i2 < id);
-                }
-            }
-            if (mine && rank < k) {
-                if (topk) topk[u * (int64_t)k + rank] = id;
-                if (rank == k - 1) {
-                    tau[u] = key_to_double(key);
-                    tid[u] = id;
-                }
-            }
-        }
-        __syncwarp();
-    }
-    kept_total = warp_sum(kept_total);
+    for (int64_t u = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; u < n; u += warps)
+        kept_total += (unsigned long long)exact_user(x, grid, cand, cand_cnt, lfin_key, cap, nseg, item_perm, k, keys,
+                                                     kid, tau, tid, topk, st, u, lane);
     if (lane == 0 && kept_total) atomicAdd(&st->cand_total, kept_total);
 }
 
-__global__ void k_band_rescore(ExactData x, const int2* __restrict__ band, unsigned band_cap,
-                               const int* __restrict__ item_perm, const double* __restrict__ tau,
-                               const int* __restrict__ tid, bool new_items, int* __restrict__ counts,
-                               DevStatus* st) {
+// The same over the users of many problems: global user g belongs to the last job whose
+// user_begin is <= g.
+__global__ void __launch_bounds__(256, 6) k_exact_tau_multi(const BatchJob* __restrict__ jobs, int count,
+                                                            int64_t total_users) {
+    const int lane = threadIdx.x & 31;
+    const int64_t warps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    unsigned long long kept_total = 0;
+    int cur = -1;
+    for (int64_t g = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; g < total_users; g += warps) {
+        int lo = 0, hi = count;
+        while (hi - lo > 1) {
+            const int mid = (lo + hi) >> 1;
+            if (jobs[mid].user_begin <= g) lo = mid; else hi = mid;
+        }
+        if (lo != cur) {
+            if (lane == 0 && cur >= 0 && kept_total) atomicAdd(&jobs[cur].st->cand_total, kept_total);
+            kept_total = 0;
+            cur = lo;
+        }
+        const BatchJob& J = jobs[lo];
+        const bool grid = *J.x.off_grid == 0u;
+        kept_total += (unsigned long long)exact_user(J.x, grid, J.cand, J.cand_cnt, J.lfin, J.cap, J.nseg,
+                                                     J.item_perm, J.k, J.keys, J.kid, J.tau, J.tid, nullptr, J.st,
+                                                     g - J.user_begin, lane);
+    }
+    if (lane == 0 && cur >= 0 && kept_total) atomicAdd(&jobs[cur].st->cand_total, kept_total);
+}
+
+// Exact membership of band pairs [st->band_done, min(st->band_count, cap)) taken with
+// stride `stride` from `first`; members add one to their item's count.
+__device__ __forceinline__ void band_pairs(const ExactData& x, const int2* __restrict__ band, unsigned band_cap,
+                                           const int* __restrict__ item_perm, const double* __restrict__ tau,
+                                           const int* __restrict__ tid, bool new_items, int* __restrict__ counts,
+                                           const DevStatus* st, unsigned first, unsigned stride) {
     const bool grid = *x.off_grid == 0u;
     const unsigned begin = st->band_done;
     unsigned end = st->band_count;
     if (end > band_cap) end = band_cap;
-    for (unsigned e = begin + blockIdx.x * blockDim.x + threadIdx.x; e < end; e += gridDim.x * blockDim.x) {
+    for (unsigned e = begin + first; e < end; e += stride) {
         const int2 b = band[e];
         const int64_t u = b.x;
         const int io = item_perm[b.y];
@@ -159,9 +240,43 @@ __global__ void k_band_rescore(ExactData x, const int2* __restrict__ band, unsig
     }
 }
 
+__global__ void k_band_rescore(ExactData x, const int2* __restrict__ band, unsigned band_cap,
+                               const int* __restrict__ item_perm, const double* __restrict__ tau,
+                               const int* __restrict__ tid, bool new_items, int* __restrict__ counts,
+                               DevStatus* st) {
+    band_pairs(x, band, band_cap, item_perm, tau, tid, new_items, counts, st, blockIdx.x * blockDim.x + threadIdx.x,
+               gridDim.x * blockDim.x);
+}
+
 __global__ void k_band_mark(DevStatus* st, unsigned band_cap) {
     unsigned end = st->band_count;
     st->band_done = end > band_cap ? band_cap : end;
+}
+
+// Band rescoring of job blockIdx.y (catalogue items: ties at tau_u are decided by t_u).
+__global__ void k_band_rescore_multi(const BatchJob* __restrict__ jobs) {
+    const BatchJob& J = jobs[blockIdx.y];
+    band_pairs(J.x, J.band, J.band_cap, J.item_perm, J.tau, J.tid, false, J.counts, J.st,
+               blockIdx.x * blockDim.x + threadIdx.x, gridDim.x * blockDim.x);
+}
+
+__global__ void k_band_mark_multi(const BatchJob* __restrict__ jobs, int count) {
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= count) return;
+    DevStatus* st = jobs[j].st;
+    const unsigned end = st->band_count, cap = jobs[j].band_cap;
+    st->band_done = end > cap ? cap : end;
+}
+
+// Zero the counts of job blockIdx.y and its band counters.
+__global__ void k_batch_reset(const BatchJob* __restrict__ jobs) {
+    const BatchJob& J = jobs[blockIdx.y];
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < J.m; i += (int64_t)gridDim.x * blockDim.x)
+        J.counts[i] = 0;
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        J.st->band_count = 0u;
+        J.st->band_done = 0u;
+    }
 }
 
 __global__ void k_histogram(const int* __restrict__ topk, int64_t nk, int* __restrict__ scores) {
@@ -212,6 +327,29 @@ void launch_band_rescore(const ExactData& x, const int2* band, unsigned band_cap
     k_band_rescore<<<1184, 256, 0, s>>>(x, band, band_cap, item_perm, tau, tid, new_items, counts, st);
     note_launch();
     k_band_mark<<<1, 1, 0, s>>>(st, band_cap);
+}
+
+void launch_exact_tau_multi(const BatchJob* jobs, int count, int64_t total_users, cudaStream_t s) {
+    if (total_users <= 0) return;
+    int64_t blocks = (total_users * 32 + 255) / 256;
+    if (blocks > 65536) blocks = 65536;
+    note_launch();
+    k_exact_tau_multi<<<(int)blocks, 256, 0, s>>>(jobs, count, total_users);
+}
+
+void launch_band_multi(const BatchJob* jobs, int count, cudaStream_t s) {
+    note_launch();
+    k_band_rescore_multi<<<dim3(64, (unsigned)count), 256, 0, s>>>(jobs);
+    note_launch();
+    k_band_mark_multi<<<(count + 127) / 128, 128, 0, s>>>(jobs, count);
+}
+
+void launch_batch_reset(const BatchJob* jobs, int count, int64_t max_m, cudaStream_t s) {
+    int64_t bx = (max_m + 255) / 256;
+    if (bx > 64) bx = 64;
+    if (bx < 1) bx = 1;
+    note_launch();
+    k_batch_reset<<<dim3((unsigned)bx, (unsigned)count), 256, 0, s>>>(jobs);
 }
 
 void launch_histogram(const int* topk, int64_t nk, int* scores, cudaStream_t s) {

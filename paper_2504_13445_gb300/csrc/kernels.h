@@ -210,7 +210,71 @@ void launch_build_units(const float* tmax, const unsigned* ucum, int t_begin, in
                         const int* t_end_dev, int tile_users, int group, int* nprefix,
                         unsigned* unit_off, DevStatus* st, cudaStream_t s);
 void launch_count_simt(const CountArgs& a, cudaStream_t s);
-void launch_count_tc(const CountArgs& a, const void* tmapA, const void* tmapB, bool fp8, cudaStream_t s);
+
+// One problem of a tensor-core counting launch: its TMA maps (users in ratio order, items
+// sorted), its arguments (its own status word, counts, band queue, unit list), and its first
+// work unit in the launch (written by launch_count_prefix).
+struct __align__(64) CountInstance {
+    CUtensorMap tmA;
+    CUtensorMap tmB;
+    CountArgs a;
+    long long unit_begin;
+};
+// inst: device array; every instance's unit list must have been built (st->units_total).
+// Writes inst[i].unit_begin and *total (device word) on the stream.
+void launch_count_prefix(CountInstance* inst, int count, unsigned long long* total, cudaStream_t s);
+// Tensor-core counting over the units of all instances (persistent, num_sms CTAs); total:
+// device word from launch_count_prefix; max_dp: largest padded depth; groups: 2 or 4.
+void launch_count_tc(const CountInstance* inst, int count, const unsigned long long* total, int max_dp, bool fp8,
+                     int groups, int num_sms, cudaStream_t s);
+
+// ---- batches: the steps after the threshold launch, one launch over all problems ----
+
+// Everything the multi-problem launches of a batch need about one problem.
+struct BatchJob {
+    // K3: exact thresholds from the candidate lists of the persistent threshold launch
+    ExactData x;                  // rows and grid codes of users and items (original order)
+    const Cand* cand;
+    const int* cand_cnt;
+    const unsigned* lfin;
+    int cap, nseg;
+    const int* item_perm;         // sorted pos -> item id
+    int64_t n, m;
+    int k, N;
+    unsigned long long* keys;
+    int* kid;
+    double* tau;
+    int* tid;
+    int64_t user_begin;           // first user of this problem in the launch's numbering
+    // K4-K6: counting stages over item tiles [0, t0) and [t0, cut)
+    const float* tmax;
+    const unsigned* ucum;
+    int tiles, t0, tile_items, group;
+    int* nprefix;
+    unsigned* unit_off;
+    int* counts;                  // by sorted position
+    int2* band;
+    unsigned band_cap;
+    // K7
+    int* top_ids_c0;
+    int* top_sc_c0;
+    int* ids;
+    int* top_scores;
+    DevStatus* st;
+};
+// jobs: device array of `count` problems, user_begin = exclusive prefix of n (total_users).
+void launch_exact_tau_multi(const BatchJob* jobs, int count, int64_t total_users, cudaStream_t s);
+// Zero every problem's counts and band counters (max_m: largest m).
+void launch_batch_reset(const BatchJob* jobs, int count, int64_t max_m, cudaStream_t s);
+// Unit lists of counting stage 1 (tiles [0, t0)) or 2 (tiles [t0, st->t_end)) of every problem.
+void launch_build_units_multi(const BatchJob* jobs, int count, int stage, cudaStream_t s);
+// Exact rescoring of every problem's new band pairs, then marks them done.
+void launch_band_multi(const BatchJob* jobs, int count, cudaStream_t s);
+// Top-N of every problem: stage 1 over the first-stage items into top_ids_c0/top_sc_c0,
+// stage 2 over the counted items into ids/top_scores.
+void launch_topn_multi(const BatchJob* jobs, int count, int stage, cudaStream_t s);
+// Filter cut of every problem from its stage-1 top-N.
+void launch_filter_cut_multi(const BatchJob* jobs, int count, cudaStream_t s);
 
 // ---- top-N (K7) ---------------------------------------------------------------------
 

@@ -405,15 +405,30 @@ __global__ void __launch_bounds__(tc_threads(NG), 1)
 
 // ---------------------------------------------------------------- K5
 
-__device__ __forceinline__ void decode_unit(const CountArgs& a, unsigned w, int len, int& T, int64_t& ut0,
-                                            int64_t& ut1) {
+// Instance of global counting unit w: the last instance whose first unit is <= w.
+__device__ __forceinline__ int count_instance(const CountInstance* inst, int count, long long w) {
+    int lo = 0, hi = count;
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (inst[mid].unit_begin <= w) lo = mid; else hi = mid;
+    }
+    return lo;
+}
+
+// Global unit w -> instance i, item tile T and user tiles [ut0, ut1) of that instance.
+__device__ __forceinline__ void decode_unit(const CountInstance* inst, int count, long long w, int& i, int& T,
+                                            int64_t& ut0, int64_t& ut1) {
+    i = count_instance(inst, count, w);
+    const CountArgs& a = inst[i].a;
+    const unsigned lw = (unsigned)(w - inst[i].unit_begin);
+    const int len = a.st->t_end - a.t_begin;
     int lo = 0, hi = len;
     while (hi - lo > 1) {
         const int mid = (lo + hi) >> 1;
-        if (a.unit_off[mid] <= w) lo = mid; else hi = mid;
+        if (a.unit_off[mid] <= lw) lo = mid; else hi = mid;
     }
     T = a.t_begin + lo;
-    const int g = (int)(w - a.unit_off[lo]);
+    const int g = (int)(lw - a.unit_off[lo]);
     const int64_t nT = a.nprefix[T];
     const int64_t all = (nT + BU - 1) / BU;
     ut0 = (int64_t)g * a.group;
@@ -421,34 +436,34 @@ __device__ __forceinline__ void decode_unit(const CountArgs& a, unsigned w, int 
     if (ut1 > all) ut1 = all;
 }
 
-// Position in a CTA's sequence of counting tiles: unit w (item tile T), user tile ut of
-// [ut0, ut1).  Units are taken as blockIdx.x, blockIdx.x + gridDim.x, ...
+// Position in a CTA's sequence of counting tiles: unit w (instance i, item tile T), user tile
+// ut of [ut0, ut1).  Units are taken as blockIdx.x, blockIdx.x + gridDim.x, ...
 struct TileCursor {
-    unsigned w;
-    int T;
+    long long w;
+    int i, T;
     int64_t ut, ut1;
     bool valid;
 };
 
-__device__ __forceinline__ void cursor_unit(const CountArgs& a, unsigned total, int len, TileCursor& c) {
+__device__ __forceinline__ void cursor_unit(const CountInstance* inst, int count, long long total, TileCursor& c) {
     c.valid = c.w < total;
     if (!c.valid) return;
     int64_t ut0;
-    decode_unit(a, c.w, len, c.T, ut0, c.ut1);
+    decode_unit(inst, count, c.w, c.i, c.T, ut0, c.ut1);
     c.ut = ut0;
 }
 
-__device__ __forceinline__ void cursor_first(const CountArgs& a, unsigned total, int len, TileCursor& c) {
+__device__ __forceinline__ void cursor_first(const CountInstance* inst, int count, long long total, TileCursor& c) {
     c.w = blockIdx.x;
-    cursor_unit(a, total, len, c);
+    cursor_unit(inst, count, total, c);
 }
 
 // Every unit holds at least one user tile, so one step never skips a unit.
-__device__ __forceinline__ void cursor_next(const CountArgs& a, unsigned total, int len, TileCursor& c) {
+__device__ __forceinline__ void cursor_next(const CountInstance* inst, int count, long long total, TileCursor& c) {
     if (!c.valid) return;
     if (++c.ut < c.ut1) return;
     c.w += gridDim.x;
-    cursor_unit(a, total, len, c);
+    cursor_unit(inst, count, total, c);
 }
 
 // Add a warp's per-item counters of the CW columns starting at pos0 to the global counts.
@@ -465,9 +480,16 @@ __device__ __forceinline__ void flush_counts(int* cw, int lane, int pos0, int64_
     __syncwarp();
 }
 
+// Counting pass over the work units of one or many problems (instances): unit w of the
+// launch belongs to the instance whose unit range holds it (ranges written on the device by
+// k_count_prefix from each instance's unit count, so the same launch serves both stages of
+// the filtered top-N and every instance of a batch).  Resident = 256 items of the unit's tile,
+// streamed = the unit's 128-user tiles; the TMA maps of each instance are read from the
+// instance array in global memory.  Bounded waits record a timeout in the first instance's
+// status word.
 template <bool FP8, int NG>
 __global__ void __launch_bounds__(tc_threads(NG), 1)
-    k_count_tc(const CountArgs a, const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
+    k_count_tc(const CountInstance* __restrict__ inst, int count, const unsigned long long* __restrict__ total_dev,
                const TcLayout L) {
     using Op = Operand<FP8>;
     extern __shared__ uint8_t smem_raw[];
@@ -477,10 +499,9 @@ __global__ void __launch_bounds__(tc_threads(NG), 1)
     int* cnt_all = reinterpret_cast<int*>(sm + L.aux_off);
     TcBars* B = reinterpret_cast<TcBars*>(sm + L.bar_off);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int KB = a.dp >> Op::KSHIFT;
     const int S = L.slots;
-    const unsigned total = a.st->units_total;
-    const int len = a.st->t_end - a.t_begin;
+    const long long total = (long long)*total_dev;
+    DevStatus* st0 = inst[0].a.st;
     volatile int* abort = &B->abort;
 
     setup(B, S, warp, 2 * NG);
@@ -488,33 +509,41 @@ __global__ void __launch_bounds__(tc_threads(NG), 1)
 
     if (warp == 0) {
         if (lane == 0) {
-            tma_prefetch_desc(&tmA);
-            tma_prefetch_desc(&tmB);
             int slot = 0;
             uint32_t ph = 0;
             int issued[MAX_SLOTS] = {0, 0, 0, 0};
             int res_loads = 0;
             bool ok = true;
+            int last_i = -1;
             unsigned long long pairs = 0;
-            for (unsigned w = blockIdx.x; w < total && ok; w += gridDim.x) {
-                int T;
+            for (long long w = blockIdx.x; w < total && ok; w += gridDim.x) {
+                int i, T;
                 int64_t ut0, ut1;
-                decode_unit(a, w, len, T, ut0, ut1);
+                decode_unit(inst, count, w, i, T, ut0, ut1);
+                const CountInstance& I = inst[i];
+                if (i != last_i) {
+                    if (pairs && last_i >= 0) atomicAdd(&inst[last_i].a.st->pairs_evaluated, pairs);
+                    pairs = 0;
+                    last_i = i;
+                    tma_prefetch_desc(&I.tmA);
+                    tma_prefetch_desc(&I.tmB);
+                }
+                const int KB = I.a.dp >> Op::KSHIFT;
                 const int rb = res_loads % L.nres, ru = res_loads / L.nres;
-                if (ru > 0 && !mbar_wait(&B->res_empty[rb], (ru - 1) & 1, abort, a.st)) break;
+                if (ru > 0 && !mbar_wait(&B->res_empty[rb], (ru - 1) & 1, abort, st0)) break;
                 uint8_t* dst = sB + rb * L.res_bytes;
                 mbar_expect_tx(&B->res_full[rb], KB * KB_BYTES_I);
                 for (int kb = 0; kb < KB; ++kb)
-                    tma_load_2d(dst + kb * KB_BYTES_I, &tmB, &B->res_full[rb], kb * Op::KELEMS, T * BI_TC);
+                    tma_load_2d(dst + kb * KB_BYTES_I, &I.tmB, &B->res_full[rb], kb * Op::KELEMS, T * BI_TC);
                 ++res_loads;
                 for (int64_t ut = ut0; ut < ut1 && ok; ++ut) {
                     for (int kb = 0; kb < KB; ++kb) {
-                        if (!mbar_wait(&B->empty[slot], ph ^ 1u, abort, a.st)) {
+                        if (!mbar_wait(&B->empty[slot], ph ^ 1u, abort, st0)) {
                             ok = false;
                             break;
                         }
                         mbar_expect_tx(&B->full[slot], KB_BYTES_U);
-                        tma_load_2d(ring + slot * KB_BYTES_U, &tmA, &B->full[slot], kb * Op::KELEMS, (int)(ut * BU));
+                        tma_load_2d(ring + slot * KB_BYTES_U, &I.tmA, &B->full[slot], kb * Op::KELEMS, (int)(ut * BU));
                         ++issued[slot];
                         if (++slot == S) {
                             slot = 0;
@@ -522,15 +551,15 @@ __global__ void __launch_bounds__(tc_threads(NG), 1)
                         }
                     }
                 }
-                const int64_t uend = (ut1 * BU < a.n) ? ut1 * BU : a.n;
+                const int64_t uend = (ut1 * BU < I.a.n) ? ut1 * BU : I.a.n;
                 if (ut1 > ut0) pairs += (unsigned long long)(uend - ut0 * BU) * BI_TC;
             }
-            if (pairs) atomicAdd(&a.st->pairs_evaluated, pairs);
+            if (pairs && last_i >= 0) atomicAdd(&inst[last_i].a.st->pairs_evaluated, pairs);
             for (int s = 0; s < S; ++s)
-                if (issued[s] > 0) drain_wait(&B->full[s], (uint32_t)(issued[s] - 1) & 1u, a.st);
+                if (issued[s] > 0) drain_wait(&B->full[s], (uint32_t)(issued[s] - 1) & 1u, st0);
             for (int rb = 0; rb < L.nres; ++rb) {
                 const int loads = res_loads / L.nres + (rb < res_loads % L.nres ? 1 : 0);
-                if (loads > 0) drain_wait(&B->res_full[rb], (uint32_t)(loads - 1) & 1u, a.st);
+                if (loads > 0) drain_wait(&B->res_full[rb], (uint32_t)(loads - 1) & 1u, st0);
             }
         }
     } else if (warp == 1) {
@@ -540,24 +569,25 @@ __global__ void __launch_bounds__(tc_threads(NG), 1)
             uint32_t ph = 0, tile_j = 0;
             int iter = 0;
             bool ok = true;
-            for (unsigned w = blockIdx.x; w < total && ok; w += gridDim.x, ++iter) {
-                int T;
+            for (long long w = blockIdx.x; w < total && ok; w += gridDim.x, ++iter) {
+                int i, T;
                 int64_t ut0, ut1;
-                decode_unit(a, w, len, T, ut0, ut1);
+                decode_unit(inst, count, w, i, T, ut0, ut1);
+                const int KB = inst[i].a.dp >> Op::KSHIFT;
                 const int rb = iter % L.nres;
-                if (!mbar_wait(&B->res_full[rb], (iter / L.nres) & 1, abort, a.st)) break;
+                if (!mbar_wait(&B->res_full[rb], (iter / L.nres) & 1, abort, st0)) break;
                 tc_fence_after();
                 const uint8_t* sBr = sB + rb * L.res_bytes;
                 for (int64_t ut = ut0; ut < ut1 && ok; ++ut) {
                     const uint32_t b = tile_j & 1u, use = tile_j >> 1;
-                    if (!mbar_wait(&B->tempty[b], (use & 1u) ^ 1u, abort, a.st)) {
+                    if (!mbar_wait(&B->tempty[b], (use & 1u) ^ 1u, abort, st0)) {
                         ok = false;
                         break;
                     }
                     tc_fence_after();
                     const uint32_t d = tmem + b * BI_TC;
                     for (int kb = 0; kb < KB; ++kb) {
-                        if (!mbar_wait(&B->full[slot], ph, abort, a.st)) {
+                        if (!mbar_wait(&B->full[slot], ph, abort, st0)) {
                             ok = false;
                             break;
                         }
@@ -581,7 +611,7 @@ __global__ void __launch_bounds__(tc_threads(NG), 1)
                 tc_commit(&B->res_empty[rb]);
             }
             tc_commit(&B->drain);
-            drain_wait(&B->drain, 0u, a.st);
+            drain_wait(&B->drain, 0u, st0);
         }
     } else {
         constexpr int CW = 2 * BI_TC / NG;  // accumulator columns a group reads per tile
@@ -598,27 +628,30 @@ __global__ void __launch_bounds__(tc_threads(NG), 1)
         // the current one, `nxt` the one after it, whose per-user record is loaded one tile
         // ahead so that its latency hides behind the current tile.
         TileCursor cur;
-        cursor_first(a, total, len, cur);
-        if (h == 1) cursor_next(a, total, len, cur);
+        cursor_first(inst, count, total, cur);
+        if (h == 1) cursor_next(inst, count, total, cur);
         TileCursor nxt = cur;
-        cursor_next(a, total, len, nxt);
-        cursor_next(a, total, len, nxt);
+        cursor_next(inst, count, total, nxt);
+        cursor_next(inst, count, total, nxt);
         UserMeta um_cur{}, um_nxt{};
-        if (cur.valid && cur.ut * BU + r < a.n) um_cur = a.meta[cur.ut * BU + r];
+        if (cur.valid && cur.ut * BU + r < inst[cur.i].a.n) um_cur = inst[cur.i].a.meta[cur.ut * BU + r];
         uint32_t use = 0;
-        int curT = -1;
+        int curT = -1, curI = -1;
         float pnh = 0.f, pd = 0.f;
         int te = 0;
         while (cur.valid) {
-            if (nxt.valid && nxt.ut * BU + r < a.n) um_nxt = a.meta[nxt.ut * BU + r];
-            if (cur.T != curT) {
-                if (curT >= 0) flush_counts<CW>(cw, lane, curT * BI_TC + cg, a.m, a.counts);
+            if (nxt.valid && nxt.ut * BU + r < inst[nxt.i].a.n) um_nxt = inst[nxt.i].a.meta[nxt.ut * BU + r];
+            const CountArgs& a = inst[cur.i].a;
+            if (cur.T != curT || cur.i != curI) {
+                if (curT >= 0)
+                    flush_counts<CW>(cw, lane, curT * BI_TC + cg, inst[curI].a.m, inst[curI].a.counts);
                 curT = cur.T;
+                curI = cur.i;
                 pnh = a.thmax[cur.T];
                 pd = a.tdel[cur.T];
                 if constexpr (FP8) te = a.texp[cur.T];
             }
-            if (!mbar_wait(&B->tfull[h], use & 1u, abort, a.st)) break;
+            if (!mbar_wait(&B->tfull[h], use & 1u, abort, st0)) break;
             __syncwarp();
             tc_fence_after();
             const int64_t us = cur.ut * BU + r;
@@ -666,12 +699,38 @@ __global__ void __launch_bounds__(tc_threads(NG), 1)
             ++use;
             cur = nxt;
             um_cur = um_nxt;
-            cursor_next(a, total, len, nxt);
-            cursor_next(a, total, len, nxt);
+            cursor_next(inst, count, total, nxt);
+            cursor_next(inst, count, total, nxt);
         }
-        if (curT >= 0) flush_counts<CW>(cw, lane, curT * BI_TC + cg, a.m, a.counts);
+        if (curT >= 0) flush_counts<CW>(cw, lane, curT * BI_TC + cg, inst[curI].a.m, inst[curI].a.counts);
     }
     teardown(B, warp);
+}
+
+// First global unit of every instance of a counting launch (exclusive scan of the unit
+// counts that k_build_units left in each instance's status word) and the launch's total.
+__global__ void k_count_prefix(CountInstance* inst, int count, unsigned long long* total) {
+    constexpr int T = 1024;
+    __shared__ unsigned long long part[T];
+    const int t = threadIdx.x;
+    const int per = (count + T - 1) / T;
+    const int b0 = t * per, b1 = (b0 + per < count) ? b0 + per : count;
+    unsigned long long local = 0;
+    for (int i = b0; i < b1; ++i) local += inst[i].a.st->units_total;
+    part[t] = local;
+    __syncthreads();
+    for (int o = 1; o < T; o <<= 1) {
+        const unsigned long long v = (t >= o) ? part[t - o] : 0ull;
+        __syncthreads();
+        part[t] += v;
+        __syncthreads();
+    }
+    unsigned long long run = part[t] - local;
+    for (int i = b0; i < b1; ++i) {
+        inst[i].unit_begin = (long long)run;
+        run += inst[i].a.st->units_total;
+    }
+    if (t == T - 1) *total = part[T - 1];
 }
 
 // ---------------------------------------------------------------- guard-band check
@@ -926,26 +985,31 @@ void launch_products_tc(const ProductsArgs& a, const void* tmapA, const void* tm
 namespace {
 
 template <bool FP8, int NG>
-void launch_count_ng(const CountArgs& a, const CUtensorMap& mA, const CUtensorMap& mB, cudaStream_t s) {
-    const int KB = FP8 ? a.dp / 128 : a.dp / 64;
+void launch_count_ng(const CountInstance* inst, int count, const unsigned long long* total, int max_dp, int grid,
+                     cudaStream_t s) {
+    const int KB = FP8 ? max_dp / 128 : max_dp / 64;
     // per-warp member counters: 4 NG warps x (512 / NG) columns
     const TcLayout L = make_layout(KB * KB_BYTES_I, KB_BYTES_U, 4u * NG * (2u * BI_TC / NG) * 4u, MAX_SLOTS);
     cudaFuncSetAttribute(k_count_tc<FP8, NG>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.bytes);
-    k_count_tc<FP8, NG><<<a.num_sms, tc_threads(NG), L.bytes, s>>>(a, mA, mB, L);
+    k_count_tc<FP8, NG><<<grid, tc_threads(NG), L.bytes, s>>>(inst, count, total, L);
 }
 
 }  // namespace
 
-void launch_count_tc(const CountArgs& a, const void* tmapA, const void* tmapB, bool fp8, cudaStream_t s) {
-    const CUtensorMap& mA = *static_cast<const CUtensorMap*>(tmapA);
-    const CUtensorMap& mB = *static_cast<const CUtensorMap*>(tmapB);
+void launch_count_prefix(CountInstance* inst, int count, unsigned long long* total, cudaStream_t s) {
+    note_launch();
+    k_count_prefix<<<1, 1024, 0, s>>>(inst, count, total);
+}
+
+void launch_count_tc(const CountInstance* inst, int count, const unsigned long long* total, int max_dp, bool fp8,
+                     int groups, int num_sms, cudaStream_t s) {
     note_launch();
     if (fp8) {
-        if (a.groups == 4) launch_count_ng<true, 4>(a, mA, mB, s);
-        else launch_count_ng<true, 2>(a, mA, mB, s);
+        if (groups == 4) launch_count_ng<true, 4>(inst, count, total, max_dp, num_sms, s);
+        else launch_count_ng<true, 2>(inst, count, total, max_dp, num_sms, s);
     } else {
-        if (a.groups == 4) launch_count_ng<false, 4>(a, mA, mB, s);
-        else launch_count_ng<false, 2>(a, mA, mB, s);
+        if (groups == 4) launch_count_ng<false, 4>(inst, count, total, max_dp, num_sms, s);
+        else launch_count_ng<false, 2>(inst, count, total, max_dp, num_sms, s);
     }
 }
 

@@ -18,82 +18,107 @@ __device__ __forceinline__ unsigned long long topn_key(const int* counts, const 
     return ((unsigned long long)(unsigned)counts[pos] << 32) | (unsigned long long)(0xFFFFFFFFu - id);
 }
 
-__global__ void __launch_bounds__(TOPN_THREADS) k_topn(const int* __restrict__ counts,
-                                                       const int* __restrict__ item_id, int64_t m,
-                                                       const int* m_lim_dev, int N, int* __restrict__ ids,
-                                                       int* __restrict__ scores, DevStatus* st) {
-    __shared__ unsigned hist[256];
-    __shared__ unsigned long long s_prefix;
-    __shared__ unsigned s_need;
-    __shared__ unsigned s_sel;
-    __shared__ unsigned long long sel[NMAX_TOPN];
+// Shared memory of one top-N select (one CTA of TOPN_THREADS threads).
+struct TopnSmem {
+    unsigned hist[256];
+    unsigned long long prefix;
+    unsigned need;
+    unsigned sel_count;
+    unsigned long long sel[NMAX_TOPN];
+};
+
+// Top N of positions [0, M) (all threads of the CTA call it).
+__device__ __forceinline__ void topn_select(TopnSmem& sm, const int* __restrict__ counts,
+                                            const int* __restrict__ item_id, int64_t M, int N, int* __restrict__ ids,
+                                            int* __restrict__ scores, DevStatus* st) {
     const int t = threadIdx.x;
-    int64_t M = m;
-    if (m_lim_dev) {
-        const int64_t lim = *m_lim_dev;
-        if (lim < M) M = lim;
-    }
     if (M < N || N > NMAX_TOPN) {
         if (t == 0) st->internal_error = 1u;
         return;
     }
     if (t == 0) {
-        s_prefix = 0ull;
-        s_need = (unsigned)N;
-        s_sel = 0u;
+        sm.prefix = 0ull;
+        sm.need = (unsigned)N;
+        sm.sel_count = 0u;
     }
     unsigned long long mask = 0ull;
     for (int shift = 56; shift >= 0; shift -= 8) {
-        for (int b = t; b < 256; b += TOPN_THREADS) hist[b] = 0u;
+        for (int b = t; b < 256; b += TOPN_THREADS) sm.hist[b] = 0u;
         __syncthreads();
-        const unsigned long long prefix = s_prefix;
+        const unsigned long long prefix = sm.prefix;
         for (int64_t p = t; p < M; p += TOPN_THREADS) {
             const unsigned long long key = topn_key(counts, item_id, p);
-            if ((key & mask) == prefix) atomicAdd(&hist[(key >> shift) & 255u], 1u);
+            if ((key & mask) == prefix) atomicAdd(&sm.hist[(key >> shift) & 255u], 1u);
         }
         __syncthreads();
         if (t == 0) {
-            unsigned need = s_need, cum = 0u;
+            unsigned need = sm.need, cum = 0u;
             int dg = 255;
             for (; dg > 0; --dg) {
-                if (cum + hist[dg] >= need) break;
-                cum += hist[dg];
+                if (cum + sm.hist[dg] >= need) break;
+                cum += sm.hist[dg];
             }
-            s_need = need - cum;
-            s_prefix = prefix | ((unsigned long long)dg << shift);
+            sm.need = need - cum;
+            sm.prefix = prefix | ((unsigned long long)dg << shift);
         }
         mask |= (0xFFull << shift);
         __syncthreads();
     }
-    // s_prefix is now the N-th largest key; keys are unique, so exactly N keys are >= it.
-    const unsigned long long kth = s_prefix;
+    // sm.prefix is now the N-th largest key; keys are unique, so exactly N keys are >= it.
+    const unsigned long long kth = sm.prefix;
     for (int64_t p = t; p < M; p += TOPN_THREADS) {
         const unsigned long long key = topn_key(counts, item_id, p);
         if (key >= kth) {
-            const unsigned slot = atomicAdd(&s_sel, 1u);
-            if (slot < (unsigned)NMAX_TOPN) sel[slot] = key;
+            const unsigned slot = atomicAdd(&sm.sel_count, 1u);
+            if (slot < (unsigned)NMAX_TOPN) sm.sel[slot] = key;
         }
     }
     __syncthreads();
-    if (s_sel != (unsigned)N) {
+    if (sm.sel_count != (unsigned)N) {
         if (t == 0) st->internal_error = 1u;
         return;
     }
     for (int j = t; j < N; j += TOPN_THREADS) {
-        const unsigned long long key = sel[j];
+        const unsigned long long key = sm.sel[j];
         int rank = 0;
-        for (int r = 0; r < N; ++r) rank += sel[r] > key;
+        for (int r = 0; r < N; ++r) rank += sm.sel[r] > key;
         ids[rank] = (int)(0xFFFFFFFFu - (unsigned)(key & 0xFFFFFFFFull));
         scores[rank] = (int)(key >> 32);
     }
 }
 
-// One thread: LB = N-th score of the first stage; cut at the first tile whose Eq. 2 bound
-// (users in ratio buckets up to the tile's largest norm) is below LB.  The bound of a
-// tile never increases along the norm order, so a binary search applies.
-__global__ void k_filter_cut(const int* __restrict__ top_scores_c0, int N, const float* __restrict__ tmax,
-                             const unsigned* __restrict__ ucum, int64_t tiles, int t_begin, int tile_items,
-                             int64_t m, DevStatus* st) {
+__global__ void __launch_bounds__(TOPN_THREADS) k_topn(const int* __restrict__ counts,
+                                                       const int* __restrict__ item_id, int64_t m,
+                                                       const int* m_lim_dev, int N, int* __restrict__ ids,
+                                                       int* __restrict__ scores, DevStatus* st) {
+    __shared__ TopnSmem sm;
+    int64_t M = m;
+    if (m_lim_dev) {
+        const int64_t lim = *m_lim_dev;
+        if (lim < M) M = lim;
+    }
+    topn_select(sm, counts, item_id, M, N, ids, scores, st);
+}
+
+// Top N of job blockIdx.x: stage 1 over the first-stage items, stage 2 over the counted ones.
+__global__ void __launch_bounds__(TOPN_THREADS) k_topn_multi(const BatchJob* __restrict__ jobs, int stage) {
+    __shared__ TopnSmem sm;
+    const BatchJob& J = jobs[blockIdx.x];
+    if (stage == 1) {
+        const int64_t m0 = (int64_t)J.t0 * J.tile_items;
+        topn_select(sm, J.counts, J.item_perm, m0 < J.m ? m0 : J.m, J.N, J.top_ids_c0, J.top_sc_c0, J.st);
+    } else {
+        const int64_t lim = J.st->m_counted;
+        topn_select(sm, J.counts, J.item_perm, lim < J.m ? lim : J.m, J.N, J.ids, J.top_scores, J.st);
+    }
+}
+
+// LB = N-th score of the first stage; cut at the first tile whose Eq. 2 bound (users in
+// ratio buckets up to the tile's largest norm) is below LB.  The bound of a tile never
+// increases along the norm order, so a binary search applies.
+__device__ __forceinline__ void filter_cut(const int* __restrict__ top_scores_c0, int N,
+                                           const float* __restrict__ tmax, const unsigned* __restrict__ ucum,
+                                           int64_t tiles, int t_begin, int tile_items, int64_t m, DevStatus* st) {
     const unsigned lb = (unsigned)top_scores_c0[N - 1];
     int64_t lo = t_begin, hi = tiles;  // answer in [t_begin, tiles]
     while (lo < hi) {
@@ -105,15 +130,28 @@ __global__ void k_filter_cut(const int* __restrict__ top_scores_c0, int N, const
     st->m_counted = (int)(mc < m ? mc : m);
 }
 
-// Single block: per item tile of [t_begin, t_end) its user prefix and work units, and
-// the exclusive scan of the units.
-__global__ void k_build_units(const float* __restrict__ tmax, const unsigned* __restrict__ ucum, int t_begin,
-                              int t_end_host, const int* t_end_dev, int tile_users, int group,
-                              int* __restrict__ nprefix, unsigned* __restrict__ unit_off, DevStatus* st) {
+__global__ void k_filter_cut(const int* __restrict__ top_scores_c0, int N, const float* __restrict__ tmax,
+                             const unsigned* __restrict__ ucum, int64_t tiles, int t_begin, int tile_items,
+                             int64_t m, DevStatus* st) {
+    filter_cut(top_scores_c0, N, tmax, ucum, tiles, t_begin, tile_items, m, st);
+}
+
+__global__ void k_filter_cut_multi(const BatchJob* __restrict__ jobs, int count) {
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= count) return;
+    const BatchJob& J = jobs[j];
+    filter_cut(J.top_sc_c0, J.N, J.tmax, J.ucum, J.tiles, J.t0, J.tile_items, J.m, J.st);
+}
+
+// Per item tile of [t_begin, t_end) its user prefix and work units, and the exclusive scan
+// of the units (one CTA of 1024 threads).
+__device__ __forceinline__ void build_units(const float* __restrict__ tmax, const unsigned* __restrict__ ucum,
+                                            int t_begin, int t_end, int tile_users, int group,
+                                            int* __restrict__ nprefix, unsigned* __restrict__ unit_off,
+                                            DevStatus* st) {
     constexpr int T = 1024;
     __shared__ unsigned part[T];
     const int t = threadIdx.x;
-    const int t_end = t_end_dev ? *t_end_dev : t_end_host;
     const int len = t_end > t_begin ? t_end - t_begin : 0;
     const int per = (len + T - 1) / T;
     const int b0 = t * per;
@@ -149,6 +187,20 @@ __global__ void k_build_units(const float* __restrict__ tmax, const unsigned* __
     }
 }
 
+__global__ void k_build_units(const float* __restrict__ tmax, const unsigned* __restrict__ ucum, int t_begin,
+                              int t_end_host, const int* t_end_dev, int tile_users, int group,
+                              int* __restrict__ nprefix, unsigned* __restrict__ unit_off, DevStatus* st) {
+    build_units(tmax, ucum, t_begin, t_end_dev ? *t_end_dev : t_end_host, tile_users, group, nprefix, unit_off, st);
+}
+
+// Unit lists of job blockIdx.x: stage 1 over tiles [0, t0), stage 2 over [t0, st->t_end).
+__global__ void k_build_units_multi(const BatchJob* __restrict__ jobs, int stage) {
+    const BatchJob& J = jobs[blockIdx.x];
+    const int t_begin = stage == 1 ? 0 : J.t0;
+    const int t_end = stage == 1 ? J.t0 : J.st->t_end;
+    build_units(J.tmax, J.ucum, t_begin, t_end, BU, J.group, J.nprefix, J.unit_off, J.st);
+}
+
 }  // namespace
 
 void launch_topn(const int* counts, const int* item_id, int64_t m, const int* m_lim_dev, int N, int* ids,
@@ -169,6 +221,21 @@ void launch_build_units(const float* tmax, const unsigned* ucum, int t_begin, in
     note_launch();
     k_build_units<<<1, 1024, 0, s>>>(tmax, ucum, t_begin, t_end, t_end_dev, tile_users, group, nprefix,
                                      unit_off, st);
+}
+
+void launch_topn_multi(const BatchJob* jobs, int count, int stage, cudaStream_t s) {
+    note_launch();
+    k_topn_multi<<<count, TOPN_THREADS, 0, s>>>(jobs, stage);
+}
+
+void launch_filter_cut_multi(const BatchJob* jobs, int count, cudaStream_t s) {
+    note_launch();
+    k_filter_cut_multi<<<(count + 127) / 128, 128, 0, s>>>(jobs, count);
+}
+
+void launch_build_units_multi(const BatchJob* jobs, int count, int stage, cudaStream_t s) {
+    note_launch();
+    k_build_units_multi<<<count, 1024, 0, s>>>(jobs, stage);
 }
 
 }  // namespace rkm
