@@ -119,7 +119,7 @@ enum {
 
 typedef struct {
     uint64_t pairs_total;       /* n*m (thresholds) plus n*m or n*q (counting)   */
-    uint64_t pairs_evaluated;   /* user-item products actually computed           */
+    uint64_t pairs_evaluated;   /* user-item products actually computed (both passes) */
     uint64_t candidates;        /* threshold-pass candidates rescored exactly     */
     uint64_t band_pairs;        /* counting-pass pairs rescored exactly           */
     uint64_t items_counted;     /* items whose score was computed (rkm_topn)      */
@@ -129,6 +129,8 @@ typedef struct {
     uint64_t kernel_launches;   /* kernels this library launched in the last call */
     uint64_t threshold_launches;/* launches of the threshold product kernel       */
     double phase_ms[RKM_PHASES];/* device time per phase (profile = 1), ms        */
+    uint64_t threshold_pairs;   /* products computed by the threshold pass (n*m less
+                                   the item tiles its Cauchy-Schwarz stop skipped)  */
 } rkm_stats;
 
 /* Fill `opts` with the defaults listed above. */

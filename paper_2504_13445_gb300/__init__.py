@@ -55,7 +55,7 @@ class Stats(ctypes.Structure):
                 ("items_counted", ctypes.c_uint64), ("retries", ctypes.c_int32),
                 ("exact_integer_path", ctypes.c_int32), ("last_ms", ctypes.c_double),
                 ("kernel_launches", ctypes.c_uint64), ("threshold_launches", ctypes.c_uint64),
-                ("phase_ms", ctypes.c_double * 8)]
+                ("phase_ms", ctypes.c_double * 8), ("threshold_pairs", ctypes.c_uint64)]
 
     PHASES = ("prep", "threshold", "exact", "bounds", "count", "band", "topn", "unused")
 

@@ -134,7 +134,11 @@ struct rkm_ctx {
     int jobs_cap = 0;
     Buf jobs_dev, bcount_dev;
     std::string tune_cache;
-    std::map<std::string, std::pair<int, int64_t>> tune;  // size bucket -> (group, first-stage items)
+    struct TuneEntry {
+        int group;        // user tiles per counting work unit
+        int64_t stage1;   // minimum items of the first counting stage
+    };
+    std::map<std::string, TuneEntry> tune;  // size bucket -> choices
     bool tune_loaded = false;
     // Batches run on an internal stream joined to the caller's stream by events, so that the
     // graph can be captured whatever stream the caller uses.
@@ -164,11 +168,6 @@ struct rkm_ctx {
         ev_pool.pop_back();
         return e;
     }
-
-    // Descriptors of the tensor-core counting launches of a call (slot 0: the first stage or
-    // the only one, slot 1: the second stage): pinned host staging and device copies.
-    CountInstance* cinst_host = nullptr;
-    Buf cinst_dev;
 
     // Descriptors of the tensor-core threshold launch: pinned host staging and device copy.
     TcInstance* inst_host = nullptr;
@@ -234,10 +233,6 @@ struct rkm_ctx {
         ev_pool.clear();
         if (inst_dev.p) cudaFree(inst_dev.p);
         inst_dev = Buf{};
-        if (cinst_dev.p) cudaFree(cinst_dev.p);
-        cinst_dev = Buf{};
-        if (cinst_host) cudaFreeHost(cinst_host);
-        cinst_host = nullptr;
         if (inst_host) cudaFreeHost(inst_host);
         inst_host = nullptr;
         inst_host_cap = 0;
@@ -689,9 +684,11 @@ rkm_status thresholds_core(rkm_ctx* c, const PathShape& ps, const float* U, int6
         CUDA_TRY(cudaMemsetAsync(&c->st->cand_overflow, 0, sizeof(unsigned), s));
         CUDA_TRY(cudaMemsetAsync(&c->st->internal_error, 0, sizeof(unsigned), s));
         CUDA_TRY(cudaMemsetAsync(&c->st->cand_total, 0, sizeof(unsigned long long), s));
+        CUDA_TRY(cudaMemsetAsync(&c->st->thr_pairs, 0, sizeof(unsigned long long), s));
     }
     if (c->st_host->internal_error) return fail(RKM_EINTERNAL, "threshold pass: fewer than k candidates");
     c->stats.candidates = c->st_host->cand_total;
+    c->stats.threshold_pairs = c->st_host->thr_pairs;  // products the threshold kernels computed
     c->stats.exact_integer_path = c->st_host->off_grid ? 0 : 1;
     return RKM_OK;
 }
@@ -742,11 +739,9 @@ rkm_status count_descriptor(const PathShape& ps, int64_t n, const UserOrder& uo,
 }
 
 // One counting stage over item tiles [t_begin, t_end) (t_end from the device if t_end_dev).
-// slot: descriptor slot of the tensor-core launch (0 or 1; distinct for the two stages of
-// one call, whose descriptors are copied before either runs).
 rkm_status count_stage(rkm_ctx* c, const PathShape& ps, int64_t n, const UserOrder& uo, const ItemSide& it,
                        bool new_items, int t_begin, int t_end, bool t_end_from_dev, const ExactData& x,
-                       const double* tau, const int* tid, int* cnt, int2* band, cudaStream_t s, int slot = 0) {
+                       const double* tau, const int* tid, int* cnt, int2* band, cudaStream_t s) {
     int* nprefix;
     unsigned* unit_off;
     TRY(c->ensure(c->nprefix, std::max<int64_t>(it.tiles, 1), &nprefix));
@@ -781,19 +776,10 @@ rkm_status count_stage(rkm_ctx* c, const PathShape& ps, int64_t n, const UserOrd
     a.st = c->st;
     a.num_sms = c->num_sms;
     if (ps.tc) {
-        if (!c->cinst_host) {
-            if (cudaMallocHost(&c->cinst_host, 2 * sizeof(CountInstance)) != cudaSuccess) {
-                cudaGetLastError();
-                c->cinst_host = nullptr;
-                return fail(RKM_ENOMEM, "pinned counting descriptors");
-            }
-        }
-        CountInstance* dev;
-        TRY(c->ensure(c->cinst_dev, 2, &dev));
-        TRY(count_descriptor(ps, n, uo, it, a, &c->cinst_host[slot]));
-        CUDA_TRY(cudaMemcpyAsync(dev + slot, c->cinst_host + slot, sizeof(CountInstance), cudaMemcpyHostToDevice, s));
-        launch_count_prefix(dev + slot, 1, &c->st->launch_units, s);
-        launch_count_tc(dev + slot, 1, &c->st->launch_units, ps.dp, ps.fp8, a.groups, c->num_sms, s);
+        TmapPair tm;
+        const int64_t n_pad = round_up(std::max<int64_t>(n, 1), BU);
+        TRY(make_tmaps(uo.pack, n_pad, it.pack, it.m_pad, ps.dp, BI_TC, ps.elem_bytes, &tm));
+        launch_count_tc(a, &tm.a, &tm.b, ps.fp8, s);
     } else {
         launch_count_simt(a, s);
     }
@@ -1068,7 +1054,7 @@ rkm_status count_enqueue(rkm_ctx* c, const PathShape& ps, int64_t n, const ItemS
             launch_topn(cnt, it.perm, m0, nullptr, N, tids_c0, tsc_c0, c->st, s);
             launch_filter_cut(tsc_c0, N, it.tmax, uo.ucum, it.tiles, t0, ps.item_tile, it.m, c->st, s);
         }
-        TRY(count_stage(c, ps, n, uo, it, false, t0, 0, true, x, tau, tid, cnt, band, s, 1));
+        TRY(count_stage(c, ps, n, uo, it, false, t0, 0, true, x, tau, tid, cnt, band, s));
         TRY(band_stage(c, it, false, x, tau, tid, cnt, band, s));
         Phase ph(c, s, RKM_PHASE_TOPN);
         launch_topn(cnt, it.perm, it.m, &c->st->m_counted, N, ids, top_scores, c->st, s);
@@ -1201,17 +1187,18 @@ rkm_status rkm_topn(rkm_ctx* c, const float* U, int64_t n, int64_t ldu, const fl
         if (c->st_host->internal_error) return fail(RKM_EINTERNAL, "top-N: device consistency check failed");
         c->stats.items_counted = (uint64_t)m;
         c->stats.pairs_total = (uint64_t)n * (uint64_t)m;
-        c->stats.pairs_evaluated = (uint64_t)n * (uint64_t)m;
+        c->stats.pairs_evaluated = c->stats.threshold_pairs;
         c->stats.last_ms = now_ms() - t0;
         return RKM_OK;
     }
     TRY(thresholds_core(c, ps, U, n, ldu, P, ldp, d, k, up, it, tau, tid, nullptr, s));
-    const uint64_t cands = c->stats.candidates;
+    const uint64_t cands = c->stats.candidates, thr_pairs = c->stats.threshold_pairs;
     TRY(scores_impl(c, ps, U, n, ldu, P, ldp, d, up, it, tau, tid, N, nullptr, ids, top_scores,
                     c->opts.filter != 0, s));
     c->stats.candidates = cands;
+    c->stats.threshold_pairs = thr_pairs;
     c->stats.pairs_total = 2ull * (uint64_t)n * (uint64_t)m;
-    c->stats.pairs_evaluated += (uint64_t)n * (uint64_t)m;
+    c->stats.pairs_evaluated += thr_pairs;
     c->stats.last_ms = now_ms() - t0;
     return RKM_OK;
 }
@@ -1579,7 +1566,6 @@ rkm_status batch_enqueue_tc(rkm_ctx* c, const rkm_instance* inst, int count, std
     CUDA_TRY(cudaMemcpyAsync(jd, J, (size_t)count * sizeof(BatchJob), cudaMemcpyHostToDevice, s));
     launch_exact_tau_multi(jd, count, users, s);
     const bool fp8 = w[0].ps.fp8;
-    const int groups = count_groups(max_dp, fp8, c->opts.epilogue_groups);
     for (int i = 0; i < count; ++i) {
         rkm_ctx* sc = c->sub[i];
         const rkm_instance& I = inst[i];
@@ -1621,7 +1607,7 @@ rkm_status batch_enqueue_tc(rkm_ctx* c, const rkm_instance* inst, int count, std
         a.nprefix = j.nprefix;
         a.unit_off = j.unit_off;
         a.group = j.group;
-        a.groups = groups;
+        a.groups = 2;  // the batch's counting launch runs two epilogue warpgroups
         a.cacc = x.ps.cacc;
         a.eabs = x.ps.eabs;
         a.counts = j.counts;
@@ -1642,7 +1628,7 @@ rkm_status batch_enqueue_tc(rkm_ctx* c, const rkm_instance* inst, int count, std
         CountInstance* ci = cd + (stage - 1) * count;
         launch_build_units_multi(jd, count, stage, s);
         launch_count_prefix(ci, count, &c->st->launch_units, s);
-        launch_count_tc(ci, count, &c->st->launch_units, max_dp, fp8, groups, c->num_sms, s);
+        launch_count_tc_multi(ci, count, &c->st->launch_units, max_dp, fp8, c->num_sms, s);
         launch_band_multi(jd, count, s);
         launch_topn_multi(jd, count, stage, s);
         if (stage == 1) launch_filter_cut_multi(jd, count, s);
@@ -1757,17 +1743,23 @@ void load_tune_table(rkm_ctx* c) {
     if (c->tune_loaded) return;
     c->tune_loaded = true;
     if (c->tune_cache.empty()) return;
+    // One bucket per line: key, work-unit size, first-stage items.
     std::ifstream f(c->tune_cache);
-    std::string key;
-    int g;
-    long long s1;
-    while (f >> key >> g >> s1) c->tune[key] = {g, (int64_t)s1};
+    std::string line;
+    while (std::getline(f, line)) {
+        std::istringstream ls(line);
+        std::string key;
+        int g = 0;
+        long long s1 = 0;
+        if (ls >> key >> g >> s1) c->tune[key] = {g, (int64_t)s1};
+    }
 }
 
 void save_tune_table(const rkm_ctx* c) {
     if (c->tune_cache.empty()) return;
     std::ofstream f(c->tune_cache);
-    for (const auto& kv : c->tune) f << kv.first << " " << kv.second.first << " " << kv.second.second << "\n";
+    for (const auto& kv : c->tune)
+        f << kv.first << " " << kv.second.group << " " << kv.second.stage1 << "\n";
 }
 
 // Time rkm_topn on this instance for each candidate and keep the fastest.
@@ -1777,35 +1769,37 @@ rkm_status tune_instance(rkm_ctx* sc, const rkm_instance& I, cudaStream_t s, Tun
     cudaEvent_t e0, e1;
     CUDA_TRY(cudaEventCreate(&e0));
     CUDA_TRY(cudaEventCreate(&e1));
+    auto run = [&](float* ms) -> rkm_status {
+        for (int rep = 0; rep < 2; ++rep) {  // the first run may grow the workspace
+            cudaEventRecord(e0, s);
+            const rkm_status r = rkm_topn(sc, I.U, I.n, I.ldu, I.P, I.m, I.ldp, I.d, I.k, I.N, I.ids, I.top_scores,
+                                          nullptr, nullptr, s);
+            cudaEventRecord(e1, s);
+            if (r != RKM_OK) return r;
+            cudaEventSynchronize(e1);
+            cudaEventElapsedTime(ms, e0, e1);
+        }
+        return RKM_OK;
+    };
     float best_ms = 1e30f;
     *best = TuneChoice{32, 8192};
+    rkm_status r = RKM_OK;
     for (int g : groups) {
         for (int64_t st1 : stages) {
             sc->count_group = g;
             sc->stage1_items = st1;
             float ms = 0.f;
-            for (int rep = 0; rep < 2; ++rep) {  // the first run may grow the workspace
-                cudaEventRecord(e0, s);
-                const rkm_status r = rkm_topn(sc, I.U, I.n, I.ldu, I.P, I.m, I.ldp, I.d, I.k, I.N, I.ids,
-                                              I.top_scores, nullptr, nullptr, s);
-                cudaEventRecord(e1, s);
-                if (r != RKM_OK) {
-                    cudaEventDestroy(e0);
-                    cudaEventDestroy(e1);
-                    return r;
-                }
-                cudaEventSynchronize(e1);
-                cudaEventElapsedTime(&ms, e0, e1);
-            }
+            if ((r = run(&ms)) != RKM_OK) break;
             if (ms < best_ms) {
                 best_ms = ms;
                 *best = TuneChoice{g, st1};
             }
         }
+        if (r != RKM_OK) break;
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
-    return RKM_OK;
+    return r;
 }
 
 }  // namespace
@@ -1848,8 +1842,8 @@ extern "C" rkm_status rkm_topn_batch(rkm_ctx* c, const rkm_instance* inst, int c
             tuned_any = true;
             f = c->tune.find(key);
         }
-        const int g = (f != c->tune.end()) ? f->second.first : 32;
-        const int64_t s1 = (f != c->tune.end()) ? f->second.second : 8192;
+        const int g = (f != c->tune.end()) ? f->second.group : 32;
+        const int64_t s1 = (f != c->tune.end()) ? f->second.stage1 : 8192;
         if (sc->count_group != g || sc->stage1_items != s1) drop_graph(c);
         sc->count_group = g;
         sc->stage1_items = s1;
@@ -1898,7 +1892,8 @@ extern "C" rkm_status rkm_topn_batch(rkm_ctx* c, const rkm_instance* inst, int c
         }
         c->stats.candidates += st.cand_total;
         c->stats.band_pairs += st.band_count;
-        c->stats.pairs_evaluated += st.pairs_evaluated + (uint64_t)inst[i].n * (uint64_t)inst[i].m;
+        c->stats.threshold_pairs += st.thr_pairs;
+        c->stats.pairs_evaluated += st.pairs_evaluated + st.thr_pairs;
         c->stats.pairs_total += 2ull * (uint64_t)inst[i].n * (uint64_t)inst[i].m;
     }
     if (redo) drop_graph(c);

@@ -36,7 +36,8 @@ struct DevStatus {
     unsigned long long cand_total;      // candidates kept for exact rescoring
     unsigned long long pairs_evaluated; // products computed by the counting pass
     unsigned long long launch_units;    // work units of the current tensor-core counting launch
-    unsigned long long pad[3];
+    unsigned long long thr_pairs;       // user-item products computed by the threshold pass
+    unsigned long long pad[2];
 };
 
 // Per-user data of the counting pass, one 32-byte record per user in ratio order:

@@ -191,19 +191,6 @@ __device__ __forceinline__ float select32(const float (&v)[32], int c) {
     return (c & 16) ? l4[1] : l4[0];
 }
 
-// x = v[base + c] for a compile-time base and a run-time c in [0, 8): a three-level select
-// tree (seven selects).
-template <int BASE>
-__device__ __forceinline__ float select8(const float (&v)[32], int c) {
-    const float a0 = (c & 1) ? v[BASE + 1] : v[BASE + 0];
-    const float a1 = (c & 1) ? v[BASE + 3] : v[BASE + 2];
-    const float a2 = (c & 1) ? v[BASE + 5] : v[BASE + 4];
-    const float a3 = (c & 1) ? v[BASE + 7] : v[BASE + 6];
-    const float b0 = (c & 2) ? a1 : a0;
-    const float b1 = (c & 2) ? a3 : a2;
-    return (c & 4) ? b1 : b0;
-}
-
 // Maxima of the four 8-column groups of a chunk.
 __device__ __forceinline__ void group_max8(const float (&v)[32], float (&g)[4]) {
 #pragma unroll
@@ -227,21 +214,6 @@ __device__ __forceinline__ unsigned hit_mask(const float (&v)[32], const float (
     return mask;
 }
 
-// Insert the hits of 8-column group Q of a chunk (bits 8Q .. 8Q+7 of mask).
-template <int Q>
-__device__ __forceinline__ void sel_group(const float (&v)[32], unsigned mask, int pos0, int64_t m, float E,
-                                          SelState& s, Cand* mycand, int cap, float* heap, int t, int k,
-                                          DevStatus* st) {
-    unsigned gm = (mask >> (8 * Q)) & 0xFFu;
-    while (gm) {
-        const int c = __ffs(gm) - 1;
-        gm &= gm - 1u;
-        const float x = select8<8 * Q>(v, c);
-        // s.thr only grows, so skipping values now below it is still sound.
-        if (x >= s.thr && pos0 + 8 * Q + c < m) sel_insert(x, pos0 + 8 * Q + c, E, s, mycand, cap, heap, t, k, st);
-    }
-}
-
 // Threshold-pass epilogue of one 32-column chunk.  Must be called by all 32 lanes of the
 // warp: the fast path is one maximum tree and one vote; 8-column groups in which some lane
 // reaches its threshold are compared element by element, and the hits are inserted one by
@@ -253,12 +225,14 @@ __device__ __forceinline__ void sel_chunk(const float (&v)[32], bool active, int
     group_max8(v, g);
     const float mx = fmax3f(g[0], g[1], fmaxf(g[2], g[3]));
     if (!__any_sync(0xffffffffu, active && mx >= s.thr)) return;
-    const unsigned mask = hit_mask(v, g, active, s.thr);
-    // Hits are taken group by group, so that a hit's value comes from its own 8 columns.
-    sel_group<0>(v, mask, pos0, m, E, s, mycand, cap, heap, t, k, st);
-    sel_group<1>(v, mask, pos0, m, E, s, mycand, cap, heap, t, k, st);
-    sel_group<2>(v, mask, pos0, m, E, s, mycand, cap, heap, t, k, st);
-    sel_group<3>(v, mask, pos0, m, E, s, mycand, cap, heap, t, k, st);
+    unsigned mask = hit_mask(v, g, active, s.thr);
+    while (mask) {
+        const int c = __ffs(mask) - 1;
+        mask &= mask - 1u;
+        const float x = select32(v, c);
+        // s.thr only grows, so skipping values now below it is still sound.
+        if (x >= s.thr && pos0 + c < m) sel_insert(x, pos0 + c, E, s, mycand, cap, heap, t, k, st);
+    }
 }
 
 // Counting-pass epilogue of one 32-column chunk; same calling rule as sel_chunk.

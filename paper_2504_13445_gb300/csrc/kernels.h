@@ -195,7 +195,7 @@ struct CountArgs {
     const float* tdel;      // per item tile: max ||p^ - p||
     const int* texp;        // per item tile: FP8 tile exponent (unused for BF16 / FP32)
     const int* nprefix;     // per item tile: users needed (ratio-order prefix length)
-    const unsigned* unit_off;  // [tiles+1] work units per item tile, exclusive scan
+    const unsigned* unit_off;  // [tiles+1] first unit of each item tile (exclusive scan)
     int t_begin;            // first item tile of the stage
     int group;              // user tiles per work unit
     int groups;             // tensor-core kernel: epilogue warpgroups (2 or 4)
@@ -223,10 +223,13 @@ struct __align__(64) CountInstance {
 // inst: device array; every instance's unit list must have been built (st->units_total).
 // Writes inst[i].unit_begin and *total (device word) on the stream.
 void launch_count_prefix(CountInstance* inst, int count, unsigned long long* total, cudaStream_t s);
+// Tensor-core counting of one problem (arguments and TMA maps passed by value; its unit list
+// built on the stream), with a.groups epilogue warpgroups.
+void launch_count_tc(const CountArgs& a, const void* tmapA, const void* tmapB, bool fp8, cudaStream_t s);
 // Tensor-core counting over the units of all instances (persistent, num_sms CTAs); total:
-// device word from launch_count_prefix; max_dp: largest padded depth; groups: 2 or 4.
-void launch_count_tc(const CountInstance* inst, int count, const unsigned long long* total, int max_dp, bool fp8,
-                     int groups, int num_sms, cudaStream_t s);
+// device word from launch_count_prefix; max_dp: largest padded depth.
+void launch_count_tc_multi(const CountInstance* inst, int count, const unsigned long long* total, int max_dp,
+                           bool fp8, int num_sms, cudaStream_t s);
 
 // ---- batches: the steps after the threshold launch, one launch over all problems ----
 

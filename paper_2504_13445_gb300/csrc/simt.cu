@@ -6,6 +6,7 @@
 #include <cuda_runtime.h>
 
 #include "common.cuh"
+#include "count_units.cuh"
 #include "epilogue.cuh"
 #include "kernels.h"
 
@@ -128,8 +129,10 @@ __global__ void __launch_bounds__(SIMT_THREADS, 1) k_threshold_simt(ThresholdArg
                 mycand = a.cand + u * (int64_t)a.nseg * a.cap;
             }
         }
+        int64_t tiles_done = 0;
         for (int64_t it = 0; it < item_tiles; ++it) {
             simt_tile(A, ut * BU, B, it * BI_SIMT, a.dp, sm);
+            bool need_next = false;
             if (owner) {
                 const float E = err_bound(a.cacc, a.eabs, un, unh, ud, a.thmax[it], a.tdel[it]);
                 s.thr = __fsub_rd(sel_bound(s), E);
@@ -140,8 +143,18 @@ __global__ void __launch_bounds__(SIMT_THREADS, 1) k_threshold_simt(ThresholdArg
                     sel_chunk(v, active, (int)(it * BI_SIMT + c0), a.m, E, s, mycand, a.cap, heap, t,
                               a.k, a.st);
                 }
+                // Algorithm 1's stop by Cauchy-Schwarz: items come in descending norm order, so
+                // once ||u|| max||p|| of the next tile (rounded up) is below a lower bound of
+                // tau_u, no later item can reach tau_u or tie it.
+                need_next = active && it + 1 < item_tiles && !(__fmul_ru(un, a.tmax[it + 1]) < sel_bound(s));
             }
-            __syncthreads();
+            ++tiles_done;
+            if (!__syncthreads_or(need_next)) break;
+        }
+        if (t == 0) {
+            const int64_t rows = (a.n - ut * BU < BU) ? a.n - ut * BU : BU;
+            const int64_t items = (tiles_done * BI_SIMT < a.m) ? tiles_done * BI_SIMT : a.m;
+            atomicAdd(&a.st->thr_pairs, (unsigned long long)(rows * items));
         }
         if (active) {
             atomicMax(&a.lfin_key[u], float_key(fmaxf(s.L, s.Lw)));
@@ -166,19 +179,9 @@ __global__ void __launch_bounds__(SIMT_THREADS, 1) k_count_simt(CountArgs a) {
         const unsigned w = s_unit;
         __syncthreads();
         if (w >= total) break;
-        // Item tile of this unit: last tile whose unit offset <= w (binary search).
-        int lo = 0, hi = a.st->t_end - a.t_begin;  // unit_off has hi+1 entries
-        while (hi - lo > 1) {
-            int mid = (lo + hi) >> 1;
-            if (a.unit_off[mid] <= w) lo = mid; else hi = mid;
-        }
-        const int T = a.t_begin + lo;
-        const int g = (int)(w - a.unit_off[lo]);
-        const int64_t nT = a.nprefix[T];
-        const int64_t ut_end_all = (nT + BU - 1) / BU;
-        const int64_t ut0 = (int64_t)g * a.group;
-        int64_t ut1 = ut0 + a.group;
-        if (ut1 > ut_end_all) ut1 = ut_end_all;
+        int T;
+        int64_t ut0, ut1;
+        decode_count_unit(a, w, T, ut0, ut1);
         if (t < BI_SIMT) cnt_s[t] = 0;
         __syncthreads();
         const float pnh = a.thmax[T], pd = a.tdel[T];

@@ -24,6 +24,7 @@
 #include <cuda_runtime.h>
 
 #include "common.cuh"
+#include "count_units.cuh"
 #include "epilogue.cuh"
 #include "kernels.h"
 #include "tc_ptx.cuh"
@@ -47,7 +48,44 @@ struct TcBars {
     uint64_t tfull[2], tempty[2];
     uint32_t tmem_base;
     int abort;
+    // Threshold pass, early end of a unit (see k_threshold_tc): the producer's end marker in
+    // the first ring slot of the tile that is not loaded, the MMA issuer's end markers for the
+    // epilogue warps, and each epilogue warp's (unit, item tiles its users still need).
+    int slot_mark[MAX_SLOTS];
+    int tmark[16];
+    unsigned long long need_pub[16];
 };
+
+// Threshold pass: the item tile at which a unit may stop.  Each epilogue warp publishes how
+// many leading item tiles its 32 users still need; a warpgroup covers all 128 users of the
+// unit, so the largest value of a group whose four warps all published for this unit bounds
+// the tiles needed, and any group's bound is valid (each uses valid lower bounds of tau_u).
+__device__ __forceinline__ int unit_stop(const TcBars* B, unsigned tag, int item_tiles, int ng) {
+    int stop = item_tiles;
+    for (int g = 0; g < ng; ++g) {
+        int mg = 0;
+        bool all = true;
+        for (int j = 0; j < 4; ++j) {
+            const unsigned long long x = *reinterpret_cast<const volatile unsigned long long*>(&B->need_pub[4 * g + j]);
+            if ((unsigned)(x >> 32) != tag) {
+                all = false;
+                break;
+            }
+            const int v = (int)(unsigned)(x & 0xffffffffull);
+            mg = v > mg ? v : mg;
+        }
+        if (all && mg < stop) stop = mg;
+    }
+    return stop;
+}
+
+// Threshold pass: tell the epilogue warps that read accumulator buffer b that the unit ended
+// (mark 1 at the position of the first tile not computed, 2 at the next position).
+__device__ __forceinline__ void post_unit_end(TcBars* B, uint32_t b, int mark, int ng) {
+    for (int g = (int)b; g < ng; g += 2)
+        for (int j = 0; j < 4; ++j) *reinterpret_cast<volatile int*>(&B->tmark[4 * g + j]) = mark;
+    mbar_arrive(&B->tfull[b]);
+}
 
 struct TcLayout {
     uint32_t res_off, ring_off, aux_off, bar_off, bytes;
@@ -169,6 +207,11 @@ __global__ void __launch_bounds__(tc_threads(NG), 1)
     // barrier so that no group can read an uninitialised entry.
     unsigned long long* Lpub = reinterpret_cast<unsigned long long*>(heaps + NG * kheap * BU);
     if (warp >= 2) Lpub[threadIdx.x - 64] = 0xFFFFFFFF00000000ull;
+    if (threadIdx.x < 16) {
+        B->need_pub[threadIdx.x] = 0xFFFFFFFF00000000ull;
+        B->tmark[threadIdx.x] = 0;
+        if (threadIdx.x < MAX_SLOTS) B->slot_mark[threadIdx.x] = 0;
+    }
 
     setup(B, S, warp, 2 * NG);
     const uint32_t tmem = B->tmem_base;
@@ -194,12 +237,31 @@ __global__ void __launch_bounds__(tc_threads(NG), 1)
                 for (int kb = 0; kb < KB; ++kb)
                     tma_load_2d(dst + kb * KB_BYTES_U, &I.tmA, &B->res_full[rb], kb * Op::KELEMS, (int)(ut * BU));
                 ++res_loads;
+                int tiles_done = 0;
                 for (int it = 0; it < item_tiles && ok; ++it) {
+                    // Stop the unit when no user of it needs the remaining tiles (at least two
+                    // remaining, so that both end markers fall inside the unit's tile range):
+                    // the first ring slot of tile `it` then carries an end marker, no copy.
+                    if (it + 1 < item_tiles && it >= unit_stop(B, (unsigned)w, item_tiles, NG)) {
+                        if (!mbar_wait(&B->empty[slot], ph ^ 1u, abort, st)) {
+                            ok = false;
+                            break;
+                        }
+                        *reinterpret_cast<volatile int*>(&B->slot_mark[slot]) = -1;
+                        mbar_arrive(&B->full[slot]);
+                        ++issued[slot];
+                        if (++slot == S) {
+                            slot = 0;
+                            ph ^= 1u;
+                        }
+                        break;
+                    }
                     for (int kb = 0; kb < KB; ++kb) {
                         if (!mbar_wait(&B->empty[slot], ph ^ 1u, abort, st)) {
                             ok = false;
                             break;
                         }
+                        if (kb == 0) *reinterpret_cast<volatile int*>(&B->slot_mark[slot]) = 0;
                         mbar_expect_tx(&B->full[slot], KB_BYTES_I);
                         tma_load_2d(ring + slot * KB_BYTES_I, &I.tmB, &B->full[slot], kb * Op::KELEMS, it * BI_TC);
                         ++issued[slot];
@@ -208,7 +270,11 @@ __global__ void __launch_bounds__(tc_threads(NG), 1)
                             ph ^= 1u;
                         }
                     }
+                    ++tiles_done;
                 }
+                const int64_t urows = (I.a.n - ut * BU < BU) ? I.a.n - ut * BU : BU;
+                const int64_t done_items = ((int64_t)tiles_done * BI_TC < I.a.m) ? (int64_t)tiles_done * BI_TC : I.a.m;
+                atomicAdd(&st->thr_pairs, (unsigned long long)(urows * done_items));
             }
             // Copies in flight complete on their barriers; wait for them before the CTA exits.
             for (int s = 0; s < S; ++s)
@@ -242,9 +308,32 @@ __global__ void __launch_bounds__(tc_threads(NG), 1)
                         break;
                     }
                     tc_fence_after();
+                    if (!mbar_wait(&B->full[slot], ph, abort, st)) {
+                        ok = false;
+                        break;
+                    }
+                    if (*reinterpret_cast<volatile int*>(&B->slot_mark[slot]) < 0) {
+                        // The producer ended the unit here: release the marker's slot and pass
+                        // the end to the epilogue warps of both accumulator buffers.
+                        mbar_arrive(&B->empty[slot]);
+                        if (++slot == S) {
+                            slot = 0;
+                            ph ^= 1u;
+                        }
+                        post_unit_end(B, b, 1, NG);
+                        ++tile_j;
+                        const uint32_t b2 = tile_j & 1u, use2 = tile_j >> 1;
+                        if (!mbar_wait(&B->tempty[b2], (use2 & 1u) ^ 1u, abort, st)) {
+                            ok = false;
+                            break;
+                        }
+                        post_unit_end(B, b2, 2, NG);
+                        ++tile_j;
+                        break;
+                    }
                     const uint32_t d = tmem + b * BI_TC;
                     for (int kb = 0; kb < KB; ++kb) {
-                        if (!mbar_wait(&B->full[slot], ph, abort, st)) {
+                        if (kb > 0 && !mbar_wait(&B->full[slot], ph, abort, st)) {
                             ok = false;
                             break;
                         }
@@ -332,6 +421,19 @@ __global__ void __launch_bounds__(tc_threads(NG), 1)
                 }
                 __syncwarp();
                 tc_fence_after();
+                const int mk = *reinterpret_cast<volatile int*>(&B->tmark[ew]);
+                if (mk != 0) {
+                    // The unit ended early (end marker 1 or 2 of the MMA issuer, no product in
+                    // the buffer): release the buffer and continue the tile count where the
+                    // issuer did, two positions after the last computed tile.
+                    __syncwarp();
+                    if (lane == 0) {
+                        *reinterpret_cast<volatile int*>(&B->tmark[ew]) = 0;
+                        mbar_arrive(&B->tempty[b]);
+                    }
+                    if (mk == 1) ++tile_j;
+                    break;
+                }
                 const float E = err_bound(a.cacc, a.eabs, un, unh, ud, thm, tdl);
                 const float f = FP8 ? pow2i(ue + a.texp[it] - 16) : 1.f;  // descale of the FP8 product
                 // The other groups' bounds may be stale or from this unit's start (-inf):
@@ -393,6 +495,26 @@ __global__ void __launch_bounds__(tc_threads(NG), 1)
                 // The accumulator is released: admit this tile's candidates while the MMA
                 // computes the next tiles.
                 sel_merge_tile(s, mycand, heap, r, a.k, E, active);
+                // Algorithm 1's stop by Cauchy-Schwarz: items arrive in descending norm order,
+                // so once ||u|| max||p|| of a tile (rounded up) is below a lower bound of tau_u,
+                // no item of that tile or any later one can reach tau_u or tie it.  Publish how
+                // many leading tiles this warp's users still need.
+                {
+                    const float bnd = sel_bound(s);
+                    int need = 0;
+                    if (active) {
+                        int lo = it + 1, hi = item_tiles;  // first tile below the bound
+                        while (lo < hi) {
+                            const int mid = (lo + hi) >> 1;
+                            if (__fmul_ru(un, a.tmax[mid]) < bnd) hi = mid; else lo = mid + 1;
+                        }
+                        need = lo;
+                    }
+                    need = __reduce_max_sync(0xffffffffu, need);
+                    if (lane == 0)
+                        *reinterpret_cast<volatile unsigned long long*>(&B->need_pub[ew]) =
+                            ((unsigned long long)(unsigned)w << 32) | (unsigned)need;
+                }
             }
             if (active) {
                 atomicMax(&a.lfin_key[u], float_key(fmaxf(s.L, s.Lw)));
@@ -415,28 +537,27 @@ __device__ __forceinline__ int count_instance(const CountInstance* inst, int cou
     return lo;
 }
 
-// Global unit w -> instance i, item tile T and user tiles [ut0, ut1) of that instance.
-__device__ __forceinline__ void decode_unit(const CountInstance* inst, int count, long long w, int& i, int& T,
-                                            int64_t& ut0, int64_t& ut1) {
-    i = count_instance(inst, count, w);
-    const CountArgs& a = inst[i].a;
-    const unsigned lw = (unsigned)(w - inst[i].unit_begin);
-    const int len = a.st->t_end - a.t_begin;
-    int lo = 0, hi = len;
-    while (hi - lo > 1) {
-        const int mid = (lo + hi) >> 1;
-        if (a.unit_off[mid] <= lw) lo = mid; else hi = mid;
+// The problems of one counting launch: a single problem passed by value (its arguments and
+// TMA maps in the parameter space), or an array of problems in global memory.
+template <bool MULTI>
+struct CountSet {
+    const CountArgs& a0;
+    const CUtensorMap* mA0;
+    const CUtensorMap* mB0;
+    const CountInstance* inst;
+    int count;
+    __device__ __forceinline__ const CountArgs& args(int i) const { return MULTI ? inst[i].a : a0; }
+    __device__ __forceinline__ const CUtensorMap* mapA(int i) const { return MULTI ? &inst[i].tmA : mA0; }
+    __device__ __forceinline__ const CUtensorMap* mapB(int i) const { return MULTI ? &inst[i].tmB : mB0; }
+    // Global unit w -> problem i, item tile T and user tiles [ut0, ut1) of that problem.
+    __device__ __forceinline__ void decode(long long w, int& i, int& T, int64_t& ut0, int64_t& ut1) const {
+        i = MULTI ? count_instance(inst, count, w) : 0;
+        const long long first = MULTI ? inst[i].unit_begin : 0;
+        decode_count_unit(args(i), (unsigned)(w - first), T, ut0, ut1);
     }
-    T = a.t_begin + lo;
-    const int g = (int)(lw - a.unit_off[lo]);
-    const int64_t nT = a.nprefix[T];
-    const int64_t all = (nT + BU - 1) / BU;
-    ut0 = (int64_t)g * a.group;
-    ut1 = ut0 + a.group;
-    if (ut1 > all) ut1 = all;
-}
+};
 
-// Position in a CTA's sequence of counting tiles: unit w (instance i, item tile T), user tile
+// Position in a CTA's sequence of counting tiles: unit w (problem i, item tile T), user tile
 // ut of [ut0, ut1).  Units are taken as blockIdx.x, blockIdx.x + gridDim.x, ...
 struct TileCursor {
     long long w;
@@ -445,25 +566,28 @@ struct TileCursor {
     bool valid;
 };
 
-__device__ __forceinline__ void cursor_unit(const CountInstance* inst, int count, long long total, TileCursor& c) {
+template <bool MULTI>
+__device__ __forceinline__ void cursor_unit(const CountSet<MULTI>& cs, long long total, TileCursor& c) {
     c.valid = c.w < total;
     if (!c.valid) return;
     int64_t ut0;
-    decode_unit(inst, count, c.w, c.i, c.T, ut0, c.ut1);
+    cs.decode(c.w, c.i, c.T, ut0, c.ut1);
     c.ut = ut0;
 }
 
-__device__ __forceinline__ void cursor_first(const CountInstance* inst, int count, long long total, TileCursor& c) {
+template <bool MULTI>
+__device__ __forceinline__ void cursor_first(const CountSet<MULTI>& cs, long long total, TileCursor& c) {
     c.w = blockIdx.x;
-    cursor_unit(inst, count, total, c);
+    cursor_unit(cs, total, c);
 }
 
 // Every unit holds at least one user tile, so one step never skips a unit.
-__device__ __forceinline__ void cursor_next(const CountInstance* inst, int count, long long total, TileCursor& c) {
+template <bool MULTI>
+__device__ __forceinline__ void cursor_next(const CountSet<MULTI>& cs, long long total, TileCursor& c) {
     if (!c.valid) return;
     if (++c.ut < c.ut1) return;
     c.w += gridDim.x;
-    cursor_unit(inst, count, total, c);
+    cursor_unit(cs, total, c);
 }
 
 // Add a warp's per-item counters of the CW columns starting at pos0 to the global counts.
@@ -480,16 +604,31 @@ __device__ __forceinline__ void flush_counts(int* cw, int lane, int pos0, int64_
     __syncwarp();
 }
 
-// Counting pass over the work units of one or many problems (instances): unit w of the
-// launch belongs to the instance whose unit range holds it (ranges written on the device by
-// k_count_prefix from each instance's unit count, so the same launch serves both stages of
-// the filtered top-N and every instance of a batch).  Resident = 256 items of the unit's tile,
-// streamed = the unit's 128-user tiles; the TMA maps of each instance are read from the
-// instance array in global memory.  Bounded waits record a timeout in the first instance's
-// status word.
-template <bool FP8, int NG>
+// Fields of a problem the counting epilogue uses on every tile, kept in registers while the
+// epilogue stays on that problem.
+struct CountHot {
+    int64_t n, m;
+    float cacc, eabs;
+    int* counts;
+    int2* band;
+    unsigned band_cap;
+    DevStatus* st;
+};
+
+__device__ __forceinline__ CountHot count_hot(const CountArgs& a) {
+    return CountHot{a.n, a.m, a.cacc, a.eabs, a.counts, a.band, a.band_cap, a.st};
+}
+
+// Counting pass over the work units of one problem (MULTI = false: arguments and TMA maps by
+// value, units [0, st->units_total)) or of many (MULTI = true: unit w of the launch belongs to
+// the problem whose unit range holds it; the ranges are written on the device by
+// k_count_prefix from each problem's unit count, so one launch serves every instance of a
+// batch).  Resident = 256 items of the unit's tile, streamed = the unit's 128-user tiles.
+// Bounded waits record a timeout in the first problem's status word.
+template <bool FP8, int NG, bool MULTI>
 __global__ void __launch_bounds__(tc_threads(NG), 1)
-    k_count_tc(const CountInstance* __restrict__ inst, int count, const unsigned long long* __restrict__ total_dev,
+    k_count_tc(const CountArgs a0, const __grid_constant__ CUtensorMap tmA0, const __grid_constant__ CUtensorMap tmB0,
+               const CountInstance* __restrict__ inst, int count, const unsigned long long* __restrict__ total_dev,
                const TcLayout L) {
     using Op = Operand<FP8>;
     extern __shared__ uint8_t smem_raw[];
@@ -500,8 +639,9 @@ __global__ void __launch_bounds__(tc_threads(NG), 1)
     TcBars* B = reinterpret_cast<TcBars*>(sm + L.bar_off);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int S = L.slots;
-    const long long total = (long long)*total_dev;
-    DevStatus* st0 = inst[0].a.st;
+    const CountSet<MULTI> cs{a0, &tmA0, &tmB0, inst, count};
+    const long long total = MULTI ? (long long)*total_dev : (long long)a0.st->units_total;
+    DevStatus* st0 = cs.args(0).st;
     volatile int* abort = &B->abort;
 
     setup(B, S, warp, 2 * NG);
@@ -519,22 +659,24 @@ __global__ void __launch_bounds__(tc_threads(NG), 1)
             for (long long w = blockIdx.x; w < total && ok; w += gridDim.x) {
                 int i, T;
                 int64_t ut0, ut1;
-                decode_unit(inst, count, w, i, T, ut0, ut1);
-                const CountInstance& I = inst[i];
+                cs.decode(w, i, T, ut0, ut1);
+                const CountArgs& a = cs.args(i);
                 if (i != last_i) {
-                    if (pairs && last_i >= 0) atomicAdd(&inst[last_i].a.st->pairs_evaluated, pairs);
+                    if (pairs) atomicAdd(&cs.args(last_i).st->pairs_evaluated, pairs);
                     pairs = 0;
                     last_i = i;
-                    tma_prefetch_desc(&I.tmA);
-                    tma_prefetch_desc(&I.tmB);
+                    tma_prefetch_desc(cs.mapA(i));
+                    tma_prefetch_desc(cs.mapB(i));
                 }
-                const int KB = I.a.dp >> Op::KSHIFT;
+                const CUtensorMap* mA = cs.mapA(i);
+                const CUtensorMap* mB = cs.mapB(i);
+                const int KB = a.dp >> Op::KSHIFT;
                 const int rb = res_loads % L.nres, ru = res_loads / L.nres;
                 if (ru > 0 && !mbar_wait(&B->res_empty[rb], (ru - 1) & 1, abort, st0)) break;
                 uint8_t* dst = sB + rb * L.res_bytes;
                 mbar_expect_tx(&B->res_full[rb], KB * KB_BYTES_I);
                 for (int kb = 0; kb < KB; ++kb)
-                    tma_load_2d(dst + kb * KB_BYTES_I, &I.tmB, &B->res_full[rb], kb * Op::KELEMS, T * BI_TC);
+                    tma_load_2d(dst + kb * KB_BYTES_I, mB, &B->res_full[rb], kb * Op::KELEMS, T * BI_TC);
                 ++res_loads;
                 for (int64_t ut = ut0; ut < ut1 && ok; ++ut) {
                     for (int kb = 0; kb < KB; ++kb) {
@@ -543,7 +685,7 @@ __global__ void __launch_bounds__(tc_threads(NG), 1)
                             break;
                         }
                         mbar_expect_tx(&B->full[slot], KB_BYTES_U);
-                        tma_load_2d(ring + slot * KB_BYTES_U, &I.tmA, &B->full[slot], kb * Op::KELEMS, (int)(ut * BU));
+                        tma_load_2d(ring + slot * KB_BYTES_U, mA, &B->full[slot], kb * Op::KELEMS, (int)(ut * BU));
                         ++issued[slot];
                         if (++slot == S) {
                             slot = 0;
@@ -551,10 +693,10 @@ __global__ void __launch_bounds__(tc_threads(NG), 1)
                         }
                     }
                 }
-                const int64_t uend = (ut1 * BU < I.a.n) ? ut1 * BU : I.a.n;
+                const int64_t uend = (ut1 * BU < a.n) ? ut1 * BU : a.n;
                 if (ut1 > ut0) pairs += (unsigned long long)(uend - ut0 * BU) * BI_TC;
             }
-            if (pairs && last_i >= 0) atomicAdd(&inst[last_i].a.st->pairs_evaluated, pairs);
+            if (pairs && last_i >= 0) atomicAdd(&cs.args(last_i).st->pairs_evaluated, pairs);
             for (int s = 0; s < S; ++s)
                 if (issued[s] > 0) drain_wait(&B->full[s], (uint32_t)(issued[s] - 1) & 1u, st0);
             for (int rb = 0; rb < L.nres; ++rb) {
@@ -572,8 +714,8 @@ __global__ void __launch_bounds__(tc_threads(NG), 1)
             for (long long w = blockIdx.x; w < total && ok; w += gridDim.x, ++iter) {
                 int i, T;
                 int64_t ut0, ut1;
-                decode_unit(inst, count, w, i, T, ut0, ut1);
-                const int KB = inst[i].a.dp >> Op::KSHIFT;
+                cs.decode(w, i, T, ut0, ut1);
+                const int KB = cs.args(i).dp >> Op::KSHIFT;
                 const int rb = iter % L.nres;
                 if (!mbar_wait(&B->res_full[rb], (iter / L.nres) & 1, abort, st0)) break;
                 tc_fence_after();
@@ -628,23 +770,24 @@ __global__ void __launch_bounds__(tc_threads(NG), 1)
         // the current one, `nxt` the one after it, whose per-user record is loaded one tile
         // ahead so that its latency hides behind the current tile.
         TileCursor cur;
-        cursor_first(inst, count, total, cur);
-        if (h == 1) cursor_next(inst, count, total, cur);
+        cursor_first(cs, total, cur);
+        if (h == 1) cursor_next(cs, total, cur);
         TileCursor nxt = cur;
-        cursor_next(inst, count, total, nxt);
-        cursor_next(inst, count, total, nxt);
+        cursor_next(cs, total, nxt);
+        cursor_next(cs, total, nxt);
         UserMeta um_cur{}, um_nxt{};
-        if (cur.valid && cur.ut * BU + r < inst[cur.i].a.n) um_cur = inst[cur.i].a.meta[cur.ut * BU + r];
+        if (cur.valid && cur.ut * BU + r < cs.args(cur.i).n) um_cur = cs.args(cur.i).meta[cur.ut * BU + r];
         uint32_t use = 0;
         int curT = -1, curI = -1;
         float pnh = 0.f, pd = 0.f;
         int te = 0;
+        CountHot hot = count_hot(cs.args(0));
         while (cur.valid) {
-            if (nxt.valid && nxt.ut * BU + r < inst[nxt.i].a.n) um_nxt = inst[nxt.i].a.meta[nxt.ut * BU + r];
-            const CountArgs& a = inst[cur.i].a;
+            if (nxt.valid && nxt.ut * BU + r < cs.args(nxt.i).n) um_nxt = cs.args(nxt.i).meta[nxt.ut * BU + r];
             if (cur.T != curT || cur.i != curI) {
-                if (curT >= 0)
-                    flush_counts<CW>(cw, lane, curT * BI_TC + cg, inst[curI].a.m, inst[curI].a.counts);
+                if (curT >= 0) flush_counts<CW>(cw, lane, curT * BI_TC + cg, hot.m, hot.counts);
+                if (MULTI && cur.i != curI) hot = count_hot(cs.args(cur.i));
+                const CountArgs& a = cs.args(cur.i);
                 curT = cur.T;
                 curI = cur.i;
                 pnh = a.thmax[cur.T];
@@ -655,12 +798,12 @@ __global__ void __launch_bounds__(tc_threads(NG), 1)
             __syncwarp();
             tc_fence_after();
             const int64_t us = cur.ut * BU + r;
-            const bool active = us < a.n;
+            const bool active = us < hot.n;
             float hi_t = 0.f, lo_t = 0.f;
             int u_orig = 0;
             const float f = (FP8 && active) ? pow2i(fp8_exp(um_cur.uexp) + te - 16) : 1.f;  // descale of the FP8 product
             if (active) {
-                const float E = err_bound(a.cacc, a.eabs, um_cur.un, um_cur.unh, um_cur.ud, pnh, pd);
+                const float E = err_bound(hot.cacc, hot.eabs, um_cur.un, um_cur.unh, um_cur.ud, pnh, pd);
                 hi_t = __fadd_ru(um_cur.tau_hi, E);
                 lo_t = __fsub_rd(um_cur.tau_lo, E);
                 u_orig = um_cur.uorig;
@@ -678,7 +821,8 @@ __global__ void __launch_bounds__(tc_threads(NG), 1)
                     float v[32];
                     as_floats(ra, v);
                     if constexpr (FP8) scale_values(v, f);
-                    count_chunk(v, active, c0, pos0 + c0, a.m, hi_t, lo_t, cw, u_orig, a.band, a.band_cap, a.st);
+                    count_chunk(v, active, c0, pos0 + c0, hot.m, hi_t, lo_t, cw, u_orig, hot.band, hot.band_cap,
+                                hot.st);
                 }
                 __syncwarp();
                 tmem_wait_bind(rb);
@@ -687,8 +831,8 @@ __global__ void __launch_bounds__(tc_threads(NG), 1)
                     float v[32];
                     as_floats(rb, v);
                     if constexpr (FP8) scale_values(v, f);
-                    count_chunk(v, active, c0 + 32, pos0 + c0 + 32, a.m, hi_t, lo_t, cw, u_orig, a.band,
-                                a.band_cap, a.st);
+                    count_chunk(v, active, c0 + 32, pos0 + c0 + 32, hot.m, hi_t, lo_t, cw, u_orig, hot.band,
+                                hot.band_cap, hot.st);
                 }
                 __syncwarp();
                 if (c0 + 64 < CW) tmem_wait_bind(ra);
@@ -699,10 +843,10 @@ __global__ void __launch_bounds__(tc_threads(NG), 1)
             ++use;
             cur = nxt;
             um_cur = um_nxt;
-            cursor_next(inst, count, total, nxt);
-            cursor_next(inst, count, total, nxt);
+            cursor_next(cs, total, nxt);
+            cursor_next(cs, total, nxt);
         }
-        if (curT >= 0) flush_counts<CW>(cw, lane, curT * BI_TC + cg, inst[curI].a.m, inst[curI].a.counts);
+        if (curT >= 0) flush_counts<CW>(cw, lane, curT * BI_TC + cg, hot.m, hot.counts);
     }
     teardown(B, warp);
 }
@@ -934,12 +1078,13 @@ int threshold_groups(int kheap, int max_dp, bool fp8, int want) {
     return threshold_layout(4, kheap, max_dp, fp8).slots >= 2 ? 4 : 2;
 }
 
-// Four groups when the product of a tile is one K-block deep (BF16 d <= 64, FP8 d <= 128):
-// the MMA of a tile is then shortest and eight warps reading each tile kept the counting
-// pass 15 % faster at d = 64 on GB300; at two K-blocks and more the two were equal.
+// Four groups for BF16 tiles one K-block deep (d <= 64): the MMA of a tile is then shortest and
+// eight warps reading each tile made the counting pass 15 % faster at d = 64 on GB300; at two
+// K-blocks and more the two were equal.  FP8 keeps two: its descale multiplies make the
+// four-group kernel (96 registers per thread) spill, and it ran 2.7x slower.
 int count_groups(int dp, bool fp8, int want) {
     if (want == 2 || want == 4) return want;
-    return (fp8 ? dp <= 128 : dp <= 64) ? 4 : 2;
+    return (!fp8 && dp <= 64) ? 4 : 2;
 }
 
 void launch_threshold_tc(const TcInstance* inst, int count, long long total_units, int kheap, int max_dp,
@@ -984,14 +1129,14 @@ void launch_products_tc(const ProductsArgs& a, const void* tmapA, const void* tm
 
 namespace {
 
-template <bool FP8, int NG>
-void launch_count_ng(const CountInstance* inst, int count, const unsigned long long* total, int max_dp, int grid,
-                     cudaStream_t s) {
+template <bool FP8, int NG, bool MULTI>
+void launch_count_ng(const CountArgs& a0, const CUtensorMap& mA, const CUtensorMap& mB, const CountInstance* inst,
+                     int count, const unsigned long long* total, int max_dp, int grid, cudaStream_t s) {
     const int KB = FP8 ? max_dp / 128 : max_dp / 64;
     // per-warp member counters: 4 NG warps x (512 / NG) columns
     const TcLayout L = make_layout(KB * KB_BYTES_I, KB_BYTES_U, 4u * NG * (2u * BI_TC / NG) * 4u, MAX_SLOTS);
-    cudaFuncSetAttribute(k_count_tc<FP8, NG>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.bytes);
-    k_count_tc<FP8, NG><<<grid, tc_threads(NG), L.bytes, s>>>(inst, count, total, L);
+    cudaFuncSetAttribute(k_count_tc<FP8, NG, MULTI>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.bytes);
+    k_count_tc<FP8, NG, MULTI><<<grid, tc_threads(NG), L.bytes, s>>>(a0, mA, mB, inst, count, total, L);
 }
 
 }  // namespace
@@ -1001,16 +1146,28 @@ void launch_count_prefix(CountInstance* inst, int count, unsigned long long* tot
     k_count_prefix<<<1, 1024, 0, s>>>(inst, count, total);
 }
 
-void launch_count_tc(const CountInstance* inst, int count, const unsigned long long* total, int max_dp, bool fp8,
-                     int groups, int num_sms, cudaStream_t s) {
+void launch_count_tc(const CountArgs& a, const void* tmapA, const void* tmapB, bool fp8, cudaStream_t s) {
     note_launch();
+    const CUtensorMap& mA = *static_cast<const CUtensorMap*>(tmapA);
+    const CUtensorMap& mB = *static_cast<const CUtensorMap*>(tmapB);
     if (fp8) {
-        if (groups == 4) launch_count_ng<true, 4>(inst, count, total, max_dp, num_sms, s);
-        else launch_count_ng<true, 2>(inst, count, total, max_dp, num_sms, s);
+        if (a.groups == 4) launch_count_ng<true, 4, false>(a, mA, mB, nullptr, 1, nullptr, a.dp, a.num_sms, s);
+        else launch_count_ng<true, 2, false>(a, mA, mB, nullptr, 1, nullptr, a.dp, a.num_sms, s);
     } else {
-        if (groups == 4) launch_count_ng<false, 4>(inst, count, total, max_dp, num_sms, s);
-        else launch_count_ng<false, 2>(inst, count, total, max_dp, num_sms, s);
+        if (a.groups == 4) launch_count_ng<false, 4, false>(a, mA, mB, nullptr, 1, nullptr, a.dp, a.num_sms, s);
+        else launch_count_ng<false, 2, false>(a, mA, mB, nullptr, 1, nullptr, a.dp, a.num_sms, s);
     }
+}
+
+// Always two epilogue warpgroups: with the arguments read from device memory, four would
+// spill registers.
+void launch_count_tc_multi(const CountInstance* inst, int count, const unsigned long long* total, int max_dp,
+                           bool fp8, int num_sms, cudaStream_t s) {
+    note_launch();
+    CountArgs none{};
+    CUtensorMap nomap{};
+    if (fp8) launch_count_ng<true, 2, true>(none, nomap, nomap, inst, count, total, max_dp, num_sms, s);
+    else launch_count_ng<false, 2, true>(none, nomap, nomap, inst, count, total, max_dp, num_sms, s);
 }
 
 }  // namespace rkm

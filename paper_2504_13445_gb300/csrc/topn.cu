@@ -143,8 +143,14 @@ __global__ void k_filter_cut_multi(const BatchJob* __restrict__ jobs, int count)
     filter_cut(J.top_sc_c0, J.N, J.tmax, J.ucum, J.tiles, J.t0, J.tile_items, J.m, J.st);
 }
 
-// Per item tile of [t_begin, t_end) its user prefix and work units, and the exclusive scan
-// of the units (one CTA of 1024 threads).
+// Work units of a counting stage over item tiles [t_begin, t_end) (one CTA of 1024 threads).
+// Tile T needs the users of ratio-order prefix nprefix[T], i.e. ceil(nprefix[T] / tile_users)
+// user tiles, cut into groups of `group` user tiles; the units are numbered tile-major, (T, g)
+// for the groups g of tile T, and unit_off[j] is the first unit of tile t_begin + j
+// (unit_off[len] = total).  Concurrent CTAs then hold one item tile (shared through L2) and
+// stream different users.  (Numbering them group-major instead, so that concurrent CTAs
+// share user tiles, was measured on GB300: 3 % faster on 2,000,000 users, 22 % slower on
+// 500,000 and 36 % slower in the serving loop.)
 __device__ __forceinline__ void build_units(const float* __restrict__ tmax, const unsigned* __restrict__ ucum,
                                             int t_begin, int t_end, int tile_users, int group,
                                             int* __restrict__ nprefix, unsigned* __restrict__ unit_off,

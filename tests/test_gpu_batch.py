@@ -65,6 +65,10 @@ def test_batch_on_default_stream_and_with_autotune(rkm, problems, tmp_path):
         torch.cuda.synchronize()
         got = [(i.cpu().numpy(), s.cpu().numpy()) for i, s in outs]
     assert os.path.exists(cache) and open(cache).read().strip()
+    for line in open(cache).read().split("\n"):
+        if line.strip():  # bucket, work-unit size, first-stage items
+            key, g, s1 = line.split()
+            assert int(g) in (8, 16, 32) and int(s1) in (4096, 16384)
     for W, (ids, sc) in zip(ws, got):
         ids_o, sc_o = expected(W)
         np.testing.assert_array_equal(ids, ids_o)
