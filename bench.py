@@ -152,10 +152,11 @@ def measured_peaks() -> dict:
 
 
 # DRAM bytes per launch of the threshold kernel from an ncu capture (read + write, taken on a
-# 131,072-user launch and scaled by the users processed to the benchmark launch), keyed by a
-# hash of the kernel sources: when the kernel changes, the counters no longer apply (None).
+# 131,072-user launch of the same items and scaled by the users processed to the benchmark
+# launch), keyed by a hash of the kernel sources: when the kernel changes, the counters no
+# longer apply (None).
 THRESHOLD_TRAFFIC = {
-    "57eb48b5c915b117ecdd4a6f4135d95fc8617e472c9dc61f7fda6940f1f185fc": {"mf-500k": 6.07e8},
+    "a3c2544430f23e0ab0770219604ebc7702746093b9d36b8507cd0f48f46f2e93": {"mf-2m-k10": 1.127e10},
 }
 KERNEL_SOURCES = ['tc.cu', 'epilogue.cuh', 'tc_ptx.cuh', 'common.cuh']
 
