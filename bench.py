@@ -54,6 +54,8 @@ def parse():
                     help="skip the FP8 and FP32 runs on the same inputs (identical results, speedups)")
     ap.add_argument("--epilogue-groups", type=int, default=0, choices=[0, 2, 4],
                     help="warpgroups reading each accumulator tile in the tensor-core kernels (0 = auto)")
+    ap.add_argument("--no-seed-order", action="store_true",
+                    help="tensor-core threshold pass with users in input order (no seed pass)")
     ap.add_argument("--requests", type=int, default=2000, help="serve-1m: requests per offered load")
     ap.add_argument("--slots", type=int, default=2, help="serve-1m: concurrent batches of the serving loop")
     return ap.parse_args()
@@ -362,7 +364,7 @@ def run_ours(args, rank, local, world):
     P = torch.from_numpy(W.P).cuda()
     flush = torch.empty(512 << 20, dtype=torch.uint8, device="cuda")
     ctx = rkm.Context(args.precision, device=local, profile=True, scores_from_topk=args.scores == "histogram",
-                      epilogue_groups=args.epilogue_groups)
+                      epilogue_groups=args.epilogue_groups, seed_order=not args.no_seed_order)
     # The result every other path must reproduce bit for bit (top-N, tau_u, t_u).
     ref_out = [x.cpu() for x in ctx.topn(U, P, W.k, W.N, return_thresholds=True)]
     for _ in range(args.warmup):
@@ -498,7 +500,7 @@ def compare_paths(args, rkm, U, P, W, ref_out, local, main_ms, flush):
         if prec == args.precision:
             continue
         with rkm.Context(prec, device=local, profile=True, scores_from_topk=args.scores == "histogram",
-                         epilogue_groups=args.epilogue_groups) as c:
+                         epilogue_groups=args.epilogue_groups, seed_order=not args.no_seed_order) as c:
             c.topn(U, P, W.k, W.N)
             torch.cuda.synchronize()
             flush.zero_()

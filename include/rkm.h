@@ -103,6 +103,13 @@ typedef struct {
                                 pass 4 when a tile is one K-block deep (BF16 d <= 64, FP8
                                 d <= 128), else 2.  The threshold pass takes 4 only when
                                 asked and four per-user heaps of k bounds fit (k <= 32).   */
+    int seed_order;          /* tensor-core threshold pass: 1 = first a pass over the 2,048
+                                highest-norm items gives each user a lower bound of tau_u,
+                                users are grouped into tiles by bound / ||u|| and the bound
+                                seeds the selector, so each tile's Cauchy-Schwarz stop comes
+                                sooner (default; used when the items span 16 tiles or more,
+                                the users fit one launch and a tile's product is two K-blocks
+                                deep or more, i.e. BF16 d > 64); 0 = users in input order  */
 } rkm_opts;
 
 /* Phases timed when rkm_opts.profile is set (indices of rkm_stats.phase_ms). */

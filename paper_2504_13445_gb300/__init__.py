@@ -13,7 +13,8 @@ import ctypes
 import os
 
 HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(HERE, "lib", "librkm.so")
+# RKM_LIBRARY selects another build of the library (e.g. lib/librkm_debug.so).
+LIB_PATH = os.environ.get("RKM_LIBRARY") or os.path.join(HERE, "lib", "librkm.so")
 
 RKM_FP32, RKM_BF16, RKM_FP8 = 0, 1, 2
 PRECISIONS = {"fp32": RKM_FP32, "bf16": RKM_BF16, "fp8": RKM_FP8}
@@ -39,7 +40,7 @@ class Opts(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int), ("k_max", ctypes.c_int), ("cand_capacity", ctypes.c_int),
                 ("band_capacity", ctypes.c_int64), ("filter", ctypes.c_int), ("profile", ctypes.c_int),
                 ("autotune", ctypes.c_int), ("tune_cache", ctypes.c_char_p), ("scores_from_topk", ctypes.c_int),
-                ("epilogue_groups", ctypes.c_int)]
+                ("epilogue_groups", ctypes.c_int), ("seed_order", ctypes.c_int)]
 
 
 class Instance(ctypes.Structure):
@@ -162,7 +163,7 @@ def _mat(X):
 def rkm_create(precision: str = "bf16", device: int = 0, k_max: int = 64, cand_capacity: int = 0,
                band_capacity: int = 0, filter: bool = True, profile: bool = False, autotune: bool = False,
                tune_cache: str | None = None, scores_from_topk: bool = False,
-               epilogue_groups: int = 0) -> ctypes.c_void_p:
+               epilogue_groups: int = 0, seed_order: bool = True) -> ctypes.c_void_p:
     lib = load_library()
     o = Opts()
     lib.rkm_default_opts(ctypes.byref(o))
@@ -176,6 +177,7 @@ def rkm_create(precision: str = "bf16", device: int = 0, k_max: int = 64, cand_c
     o.tune_cache = tune_cache.encode() if tune_cache else None
     o.scores_from_topk = 1 if scores_from_topk else 0
     o.epilogue_groups = epilogue_groups
+    o.seed_order = 1 if seed_order else 0
     h = ctypes.c_void_p()
     _check(lib.rkm_create(ctypes.byref(h), ctypes.byref(o), device))
     return h

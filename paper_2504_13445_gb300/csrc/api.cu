@@ -99,6 +99,8 @@ struct rkm_ctx {
     Buf hist, offs;
     // threshold pass
     Buf cand, cand_cnt, lfin, keys, kid, topk_tmp;
+    // threshold pass: seed bounds and user order
+    Buf lseed, thr_perm;
     // counting pass
     Buf r_u, uperm, ucum, us_pack, us_meta, nprefix, unit_off, band, cnt_s, top_ids, top_sc, tau_tmp,
         tid_tmp;
@@ -213,7 +215,7 @@ struct rkm_ctx {
         Buf* all[] = {&topk_tmp, &u_e, &u_q, &u_n2, &u_nrm, &u_nhat, &u_del, &u_pack, &p_e, &p_q, &p_n2, &p_nrm,
                       &p_nhat, &p_del, &p_perm, &p_pack, &tmax, &thmax, &tdel, &hist, &offs, &cand,
                       &cand_cnt, &lfin, &keys, &kid, &r_u, &uperm, &ucum, &us_pack, &us_meta,
-                      &nprefix, &unit_off, &band, &cnt_s, &top_ids, &top_sc,
+                      &nprefix, &unit_off, &band, &cnt_s, &top_ids, &top_sc, &lseed, &thr_perm,
                       &tau_tmp, &tid_tmp, &res_U, &res_e, &res_q, &res_tau, &res_tid, &res_uperm, &res_ucum,
                       &res_pack, &res_meta, &q_e, &q_q,
                       &q_n2, &q_nrm, &q_nhat, &q_del, &q_perm, &q_pack, &q_tmax, &q_thmax, &q_tdel, &q_cnt,
@@ -411,6 +413,8 @@ rkm_status read_status(rkm_ctx* c, cudaStream_t s) {
     CUDA_TRY(cudaStreamSynchronize(s));
     collect_phases(c);
     if (c->st_host->timeout) return fail(RKM_ETIMEOUT, "a bounded device wait gave up (kernel aborted)");
+    if (c->st_host->debug_line)
+        return fail(RKM_EINTERNAL, "debug build: a device index check failed (source line %u)", c->st_host->debug_line);
     return RKM_OK;
 }
 
@@ -601,17 +605,19 @@ rkm_status threshold_descriptor(const PathShape& ps, const ThrPlan& pl, const It
     return RKM_OK;
 }
 
+// slot: descriptor slot (0 or 1; the seed pass and the main pass of one call use different
+// slots, since the pinned staging of the first may not have been copied yet).
 rkm_status threshold_launch_one(rkm_ctx* c, const PathShape& ps, const ThrPlan& pl, const ItemSide& it,
-                                cudaStream_t s) {
+                                cudaStream_t s, int slot = 0) {
     Phase ph(c, s, RKM_PHASE_THRESHOLD);
     c->stats.threshold_launches++;
     if (ps.tc) {
         TcInstance* hi;
         TcInstance* di;
-        TRY(c->instances(1, &hi, &di));
-        TRY(threshold_descriptor(ps, pl, it, hi));
-        CUDA_TRY(cudaMemcpyAsync(di, hi, sizeof(TcInstance), cudaMemcpyHostToDevice, s));
-        launch_threshold_tc(di, 1, (pl.a.n + BU - 1) / BU, pl.a.k, ps.dp, ps.fp8, pl.nseg, c->num_sms, s);
+        TRY(c->instances(2, &hi, &di));
+        TRY(threshold_descriptor(ps, pl, it, hi + slot));
+        CUDA_TRY(cudaMemcpyAsync(di + slot, hi + slot, sizeof(TcInstance), cudaMemcpyHostToDevice, s));
+        launch_threshold_tc(di + slot, 1, (pl.a.n + BU - 1) / BU, pl.a.k, ps.dp, ps.fp8, pl.nseg, c->num_sms, s);
     } else {
         launch_threshold_simt(pl.a, s);
     }
@@ -622,9 +628,50 @@ void threshold_exact(rkm_ctx* c, const float* U, int64_t ldu, const float* P, in
                      const RowPrep& up, const ItemSide& it, const ThrPlan& pl, double* tau, int* tid, int* topk,
                      cudaStream_t s) {
     Phase ph(c, s, RKM_PHASE_EXACT);
-    ExactData x{U, ldu, up.e, up.q, P, ldp, it.rp.e, it.rp.q, d, (int)round_up(d, 8), &c->st->off_grid};
+    ExactData x{U, ldu, up.e, up.q, P, ldp, it.rp.e, it.rp.q, d, (int)round_up(d, 8), &c->st->off_grid,
+                pl.a.n, it.m};
     launch_exact_tau(x, pl.cand, pl.cand_cnt, pl.lfin, pl.cap, pl.nseg, it.perm, pl.a.n, pl.a.k, pl.keys, pl.kid,
-                     tau, tid, topk, c->st, s);
+                     tau, tid, topk, c->st, s, pl.a.uperm);
+}
+
+// Seed order of the tensor-core threshold pass.  Items arrive in descending norm order and a
+// user tile stops once no user of it can still reach its bound (Algorithm 1's Cauchy-Schwarz
+// stop), so a tile stops as late as its user with the smallest tau_u / ||u||.  A first pass
+// of the same kernel over the SEED_TILES highest-norm item tiles gives every user a lower
+// bound L_u of tau_u (the k-th largest lower bound over those items); users are then packed
+// in the order of L_u / ||u||, so that the users of a tile stop at about the same item, and
+// L_u seeds the selector of the main pass.  The results do not depend on the order.  Used when
+// a tile's product is two K-blocks deep or more (BF16 d > 64): measured on GB300 at
+// 2M x 500K, d = 128, the products computed fell from 59 % to 52 % of n*m and the threshold
+// phase from 116 to 104 ms; at 500K x 100K, d = 64, where the epilogue bounds the kernel, the
+// phase grew from 7.9 to 8.9 ms.
+constexpr int64_t SEED_TILES = 8;
+
+rkm_status threshold_seed_order(rkm_ctx* c, const PathShape& ps, const float* U, int64_t n, int64_t ldu, int d,
+                                const RowPrep& up, const ItemSide& it, ThrPlan* pl, cudaStream_t s) {
+    unsigned *seed, *hist, *offs;
+    float* r;
+    int* perm;
+    TRY(c->ensure(c->lseed, n, &seed));
+    TRY(c->ensure(c->r_u, n, &r));
+    TRY(c->ensure(c->hist, HIST_WORDS, &hist));
+    TRY(c->ensure(c->offs, NBUCKET, &offs));
+    TRY(c->ensure(c->thr_perm, n, &perm));
+    CUDA_TRY(cudaMemsetAsync(seed, 0, n * sizeof(unsigned), s));
+    ThrPlan pre = *pl;
+    pre.a.m = std::min<int64_t>(it.m, SEED_TILES * BI_TC);
+    pre.a.lfin_key = seed;
+    TRY(threshold_launch_one(c, ps, pre, it, s, 1));
+    {
+        Phase ph(c, s, RKM_PHASE_PREP);
+        launch_seed_ratio(seed, up.nrm, n, r, s);
+        launch_bucket_sort(r, n, false, hist, offs, perm, nullptr, s);
+        TRY(pack(c, ps, U, n, ldu, d, perm, pl->n_pad, c->u_pack, &pl->apack, s, up.e));
+    }
+    pl->a.A = pl->apack;
+    pl->a.uperm = perm;
+    pl->a.lfin_seed = seed;
+    return RKM_OK;
 }
 
 // Grow the candidate capacity after an overflow; fails after three retries.
@@ -669,6 +716,9 @@ rkm_status thresholds_core(rkm_ctx* c, const PathShape& ps, const float* U, int6
             const RowPrep us = row_slice(up, u0, d);
             ThrPlan pl;
             TRY(threshold_prepare(c, ps, U + u0 * ldu, un, ldu, d, k, us, it, &pl, s));
+            if (ps.tc && c->opts.seed_order && slice >= n && it.tiles >= 2 * SEED_TILES &&
+                ps.dp * ps.elem_bytes >= 256)
+                TRY(threshold_seed_order(c, ps, U, n, ldu, d, up, it, &pl, s));
             TRY(threshold_launch_one(c, ps, pl, it, s));
             threshold_exact(c, U + u0 * ldu, ldu, P, ldp, d, us, it, pl, tau + u0, tid + u0,
                             topk ? topk + u0 * k : nullptr, s);
@@ -860,7 +910,7 @@ rkm_status rkm::query_resident(rkm_ctx* c, const rkm_ctx* r, const float* Q, int
                  static_cast<UserMeta*>(r->res_meta.p)};
     ExactData x{static_cast<const float*>(r->res_U.p), d, static_cast<const int*>(r->res_e.p),
                 static_cast<const int16_t*>(r->res_q.p), Q, ldq, it.rp.e, it.rp.q, d, (int)round_up(d, 8),
-                &c->st->off_grid};
+                &c->st->off_grid, n, q};
     int* cnt;
     TRY(c->ensure(c->q_cnt, q, &cnt));
     for (int attempt = 0;; ++attempt) {
@@ -906,6 +956,7 @@ void rkm_default_opts(rkm_opts* o) {
     o->tune_cache = nullptr;
     o->scores_from_topk = 0;
     o->epilogue_groups = 0;
+    o->seed_order = 1;
 }
 
 const char* rkm_last_error(void) { return g_err.c_str(); }
@@ -1014,7 +1065,8 @@ rkm_status count_prepare(rkm_ctx* c, const PathShape& ps, const float* U, int64_
         TRY(order_users(c, ps, U, n, ldu, d, up, tau, tid, UserBufs{c->uperm, c->ucum, c->us_pack, c->us_meta},
                         &cp->uo, s));
     }
-    cp->x = ExactData{U, ldu, up.e, up.q, P, ldp, it.rp.e, it.rp.q, d, (int)round_up(d, 8), &c->st->off_grid};
+    cp->x = ExactData{U, ldu, up.e, up.q, P, ldp, it.rp.e, it.rp.q, d, (int)round_up(d, 8), &c->st->off_grid,
+                      n, it.m};
     TRY(c->ensure(c->cnt_s, it.m, &cp->cnt));
     return RKM_OK;
 }
@@ -1541,7 +1593,7 @@ rkm_status batch_enqueue_tc(rkm_ctx* c, const rkm_instance* inst, int count, std
         BatchJob& j = J[i];
         j = BatchJob{};
         j.x = ExactData{I.U, I.ldu, x.up.e, x.up.q, I.P, I.ldp, x.it.rp.e, x.it.rp.q, I.d, (int)round_up(I.d, 8),
-                        &sc->st->off_grid};
+                        &sc->st->off_grid, I.n, I.m};
         j.cand = x.pl.cand;
         j.cand_cnt = x.pl.cand_cnt;
         j.lfin = x.pl.lfin;

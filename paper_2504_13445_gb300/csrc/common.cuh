@@ -26,7 +26,7 @@ struct DevStatus {
     unsigned int internal_error;  // a consistency check failed (e.g. < k candidates)
     unsigned int timeout;         // a bounded wait gave up
     unsigned int off_grid;        // set when a user or item row is not on the 2^-12 grid
-    unsigned int unused0;
+    unsigned int debug_line;      // debug builds: source line of the first failed index check
     unsigned int band_count;      // pairs pushed to the band queue (may exceed capacity)
     unsigned int band_done;       // pairs of the queue already rescored
     unsigned int ticket;          // work ticket of the persistent counting kernel
@@ -39,6 +39,23 @@ struct DevStatus {
     unsigned long long thr_pairs;       // user-item products computed by the threshold pass
     unsigned long long pad[2];
 };
+
+// Debug builds (-DRKM_DEBUG): index checks on the gathers and scatters whose index comes from
+// device data.  A failed check records its source line in the status word (the first one
+// wins), raises internal_error and skips the access; the call returns RKM_EINTERNAL.  Release
+// builds compile the checks away.
+#ifdef RKM_DEBUG
+__device__ __forceinline__ bool rkm_dcheck(bool ok, DevStatus* st, int line) {
+    if (!ok) {
+        atomicCAS(&st->debug_line, 0u, (unsigned)line);
+        st->internal_error = 1u;
+    }
+    return ok;
+}
+#define RKM_DCHECK(cond, st) ::rkm::rkm_dcheck((cond), (st), __LINE__)
+#else
+#define RKM_DCHECK(cond, st) true
+#endif
 
 // Per-user data of the counting pass, one 32-byte record per user in ratio order:
 // tau_u rounded up and down to FP32, ||u||, ||u^||, ||u^ - u|| (rounded up), original id.
@@ -64,6 +81,13 @@ __host__ __device__ __forceinline__ uint32_t float_key(float x) {
     memcpy(&b, &x, 4);
 #endif
     return (b & 0x80000000u) ? ~b : (b | 0x80000000u);
+}
+
+// Inverse of float_key; the key 0 (nothing recorded) reads as -inf.
+__device__ __forceinline__ float key_float(uint32_t k) {
+    if (k == 0u) return -INFINITY;
+    const uint32_t b = (k & 0x80000000u) ? (k ^ 0x80000000u) : ~k;
+    return __uint_as_float(b);
 }
 
 // 16-bit bucket of a float, monotone non-decreasing in x.

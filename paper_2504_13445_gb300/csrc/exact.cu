@@ -107,8 +107,10 @@ __device__ __forceinline__ int exact_user(const ExactData& x, bool grid, const C
                                           int cap, int nseg, const int* __restrict__ item_perm, int k,
                                           unsigned long long* __restrict__ keys, int* __restrict__ kid,
                                           double* __restrict__ tau, int* __restrict__ tid, int* __restrict__ topk,
-                                          DevStatus* st, int64_t u, int lane) {
+                                          DevStatus* st, int64_t u, int lane, const int* __restrict__ uperm) {
     const unsigned lt_mask = (1u << lane) - 1u;
+    const int64_t uo = uperm ? (int64_t)uperm[u] : u;  // row of the lists -> original user
+    if (!RKM_DCHECK(uo >= 0 && (x.n_users == 0 || uo < x.n_users), st)) return k;
     const float L = key_to_float(lfin_key[u]);
     unsigned long long* kk = keys + u * (int64_t)nseg * cap;
     int* ki = kid + u * (int64_t)nseg * cap;
@@ -124,13 +126,14 @@ __device__ __forceinline__ int exact_user(const ExactData& x, bool grid, const C
             cj.pos = 0;
             if (j < cnt) {
                 cj = c[j];
-                keep = cj.ub >= L;
+                keep = cj.ub >= L && RKM_DCHECK(cj.pos >= 0 && (x.m_items == 0 || cj.pos < x.m_items), st);
             }
             const unsigned mask = __ballot_sync(0xffffffffu, keep);
             if (keep) {
                 const int slot = kept + __popc(mask & lt_mask);
                 const int io = item_perm[cj.pos];
-                kk[slot] = double_key(exact_dot(x, grid, u, io));
+                RKM_DCHECK(io >= 0 && (x.m_items == 0 || io < x.m_items), st);
+                kk[slot] = double_key(exact_dot(x, grid, uo, io));
                 ki[slot] = io;
             }
             kept += __popc(mask);
@@ -162,10 +165,10 @@ __device__ __forceinline__ int exact_user(const ExactData& x, bool grid, const C
             }
         }
         if (mine && rank < k) {
-            if (topk) topk[u * (int64_t)k + rank] = id;
+            if (topk) topk[uo * (int64_t)k + rank] = id;
             if (rank == k - 1) {
-                tau[u] = key_to_double(key);
-                tid[u] = id;
+                tau[uo] = key_to_double(key);
+                tid[uo] = id;
             }
         }
     }
@@ -180,14 +183,14 @@ __global__ void __launch_bounds__(256, 6) k_exact_tau(ExactData x, const Cand* _
                             const int* __restrict__ item_perm,
                             int64_t n, int k, unsigned long long* __restrict__ keys,
                             int* __restrict__ kid, double* __restrict__ tau, int* __restrict__ tid,
-                            int* __restrict__ topk, DevStatus* st) {
+                            int* __restrict__ topk, DevStatus* st, const int* __restrict__ uperm) {
     const int lane = threadIdx.x & 31;
     const bool grid = *x.off_grid == 0u;
     const int64_t warps = ((int64_t)gridDim.x * blockDim.x) >> 5;
     unsigned long long kept_total = 0;
     for (int64_t u = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; u < n; u += warps)
         kept_total += (unsigned long long)exact_user(x, grid, cand, cand_cnt, lfin_key, cap, nseg, item_perm, k, keys,
-                                                     kid, tau, tid, topk, st, u, lane);
+                                                     kid, tau, tid, topk, st, u, lane, uperm);
     if (lane == 0 && kept_total) atomicAdd(&st->cand_total, kept_total);
 }
 
@@ -214,7 +217,7 @@ __global__ void __launch_bounds__(256, 6) k_exact_tau_multi(const BatchJob* __re
         const bool grid = *J.x.off_grid == 0u;
         kept_total += (unsigned long long)exact_user(J.x, grid, J.cand, J.cand_cnt, J.lfin, J.cap, J.nseg,
                                                      J.item_perm, J.k, J.keys, J.kid, J.tau, J.tid, nullptr, J.st,
-                                                     g - J.user_begin, lane);
+                                                     g - J.user_begin, lane, nullptr);
     }
     if (lane == 0 && cur >= 0 && kept_total) atomicAdd(&jobs[cur].st->cand_total, kept_total);
 }
@@ -231,6 +234,10 @@ __device__ __forceinline__ void band_pairs(const ExactData& x, const int2* __res
     if (end > band_cap) end = band_cap;
     for (unsigned e = begin + first; e < end; e += stride) {
         const int2 b = band[e];
+        if (!RKM_DCHECK(b.x >= 0 && (x.n_users == 0 || b.x < x.n_users) && b.y >= 0 &&
+                            (x.m_items == 0 || b.y < x.m_items),
+                        const_cast<DevStatus*>(st)))
+            continue;
         const int64_t u = b.x;
         const int io = item_perm[b.y];
         const double s = exact_dot(x, grid, u, io);
@@ -310,13 +317,13 @@ void launch_histogram_prefix(const int* lists, int64_t n, int kmax, int k, int64
 
 void launch_exact_tau(const ExactData& x, const Cand* cand, const int* cand_cnt, const unsigned* lfin_key,
                       int cap, int nseg, const int* item_perm, int64_t n, int k, unsigned long long* keys, int* kid,
-                      double* tau, int* tid, int* topk, DevStatus* st, cudaStream_t s) {
+                      double* tau, int* tid, int* topk, DevStatus* st, cudaStream_t s, const int* uperm) {
     if (n <= 0) return;
     int64_t blocks = (n * 32 + 255) / 256;
     if (blocks > 65536) blocks = 65536;
     note_launch();
     k_exact_tau<<<(int)blocks, 256, 0, s>>>(x, cand, cand_cnt, lfin_key, cap, nseg, item_perm, n, k, keys, kid, tau,
-                                            tid, topk, st);
+                                            tid, topk, st, uperm);
 }
 
 void launch_band_rescore(const ExactData& x, const int2* band, unsigned band_cap, const int* item_perm,

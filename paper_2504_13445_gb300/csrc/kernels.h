@@ -72,6 +72,10 @@ void launch_tile_max(const float* nrm, const float* nhat, const float* del, cons
 // K4: r_u = tau_u / ||u|| rounded down (-inf when tau_u <= 0).
 void launch_user_ratio(const double* tau, const double* norm2, int64_t n, float* r, cudaStream_t s);
 
+// Ordering key of the threshold pass: r[u] = L_u / ||u|| for a lower bound L_u of tau_u given
+// as float_key (key 0 or L_u <= 0 gives -inf).  Only an order, not a bound.
+void launch_seed_ratio(const unsigned* lkey, const float* nrm, int64_t n, float* r, cudaStream_t s);
+
 // K4: per-user records of the counting pass, in ratio order (perm: ratio order -> user).
 void launch_user_meta(const double* tau, const float* nrm, const float* nhat, const float* del, const int* ex,
                       const int* perm, int64_t n, UserMeta* meta, cudaStream_t s);
@@ -102,6 +106,12 @@ struct ThresholdArgs {
     int nseg;             // candidate segments per user (epilogue groups of the kernel)
     DevStatus* st;
     int num_sms;
+    // Tensor-core kernel, optional: the users packed in A are in this order (packed row ->
+    // original user; the per-user norms and exponents above are by original user, the outputs
+    // cand / cand_cnt / lfin_key by packed row), and a lower bound of tau_u per original
+    // user (float_key, 0 = none) that seeds the selector.
+    const int* uperm;
+    const unsigned* lfin_seed;
 };
 void launch_threshold_simt(const ThresholdArgs& a, cudaStream_t s);
 
@@ -161,13 +171,16 @@ struct ExactData {
     const int* ep; const int16_t* qp;
     int d, dq;
     const unsigned* off_grid;  // device flag: zero = every row on the grid, use the integer path
+    // Debug builds check gathered indices against these (0 = unchecked).
+    int64_t n_users = 0, m_items = 0;
 };
 
-// K3: exact tau_u, t_u and (optionally) S_k(u) from the candidate lists.
+// K3: exact tau_u, t_u and (optionally) S_k(u) from the candidate lists.  With uperm, the
+// lists are by threshold-pass row and uperm[row] is the original user (rows, outputs).
 void launch_exact_tau(const ExactData& x, const Cand* cand, const int* cand_cnt, const unsigned* lfin_key,
                       int cap, int nseg, const int* item_perm, int64_t n, int k,
                       unsigned long long* keys, int* kid, double* tau, int* tid, int* topk,
-                      DevStatus* st, cudaStream_t s);
+                      DevStatus* st, cudaStream_t s, const int* uperm = nullptr);
 
 // K6: rescore queued band pairs (orig user, sorted item pos) and add members to counts.
 void launch_band_rescore(const ExactData& x, const int2* band, unsigned band_cap,

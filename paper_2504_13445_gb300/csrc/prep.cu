@@ -440,6 +440,21 @@ void launch_tile_max(const float* nrm, const float* nhat, const float* del, cons
     }
 }
 
+__global__ void k_seed_ratio(const unsigned* __restrict__ lkey, const float* __restrict__ nrm, int64_t n,
+                             float* __restrict__ r) {
+    for (int64_t u = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; u < n; u += (int64_t)gridDim.x * blockDim.x) {
+        const float L = key_float(lkey[u]);
+        r[u] = (L > 0.f && nrm[u] > 0.f) ? L / nrm[u] : -INFINITY;
+    }
+}
+
+void launch_seed_ratio(const unsigned* lkey, const float* nrm, int64_t n, float* r, cudaStream_t s) {
+    if (n > 0) {
+        note_launch();
+        k_seed_ratio<<<grid_for(n, 256, 65536), 256, 0, s>>>(lkey, nrm, n, r);
+    }
+}
+
 void launch_user_ratio(const double* tau, const double* norm2, int64_t n, float* r, cudaStream_t s) {
     if (n > 0) {
         note_launch();

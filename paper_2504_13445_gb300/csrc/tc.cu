@@ -393,10 +393,15 @@ __global__ void __launch_bounds__(tc_threads(NG), 1)
             s.defer = 1;
             s.mark = 0;
             bool warm = false;  // warm start done for this unit
-            const float un = active ? a.unrm[u] : 0.f;
-            const float unh = active ? a.unhat[u] : 0.f;
-            const float ud = active ? a.udel[u] : 0.f;
-            const int ue = (FP8 && active) ? fp8_exp(a.uexp[u]) : 0;
+            // Packed row u holds original user uo; a seed bound of tau_u (from a pass over the
+            // highest-norm items) starts the selector above -inf.
+            const int64_t uo = (active && a.uperm) ? (int64_t)a.uperm[u] : u;
+            const float seed = (active && a.lfin_seed) ? key_float(a.lfin_seed[uo]) : -INFINITY;
+            s.Lw = seed;
+            const float un = active ? a.unrm[uo] : 0.f;
+            const float unh = active ? a.unhat[uo] : 0.f;
+            const float ud = active ? a.udel[uo] : 0.f;
+            const int ue = (FP8 && active) ? fp8_exp(a.uexp[uo]) : 0;
             Cand* mycand = a.cand + ((active ? u : 0) * a.nseg + g) * (int64_t)a.cap;
             // This group's first tile of the unit, then every other one: the bound maxima of
             // the next one are loaded while the current one is processed.
@@ -457,7 +462,7 @@ __global__ void __launch_bounds__(tc_threads(NG), 1)
                         if constexpr (FP8) scale_values(v, f);
                     };
                     const float lw = warm_bound<CW / 4, CW>(load, it * BI_TC + cg, a.m, a.k, E);
-                    s.Lw = active ? lw : -INFINITY;
+                    s.Lw = active ? fmaxf(lw, seed) : -INFINITY;
                     publish_bound(s.pub, s.tag, s.Lw);
                     warm = true;
                 }

@@ -73,3 +73,13 @@ def test_create_without_gpu_reports_error(lib):
     h = ctypes.c_void_p()
     status = lib.rkm_create(ctypes.byref(h), None, 0)
     assert status != 0 and lib.rkm_last_error()
+
+
+def test_debug_build_exports_every_declared_symbol():
+    """The RKM_DEBUG variant (device index checks on) builds from the same sources and exports
+    the same C ABI."""
+    from paper_2504_13445_gb300 import build as b
+    path = b.build(debug=True)
+    lib = ctypes.CDLL(path)
+    for name in declared_functions():
+        assert hasattr(lib, name), f"{name} missing from the debug library"

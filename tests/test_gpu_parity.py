@@ -86,6 +86,28 @@ def test_mid_size_mf_spans_many_tiles(rkm, prec):
         assert st["items_counted"] <= W.m
 
 
+@pytest.mark.parametrize("prec", ["bf16"])
+def test_threshold_seed_order_and_stop(rkm, prec):
+    """The tensor-core threshold pass with and without the seed order (a first pass over the
+    highest-norm items, users grouped by bound / ||u||): identical thresholds and S_k(u), equal
+    to the oracle's, and the Cauchy-Schwarz stop computes fewer than n*m products."""
+    W = workloads.mf(24_000, 12_000, 128, 10, 20, seed=9)  # BF16 d = 128: two K-blocks per tile
+    tau_o, tid_o, topk_o = oracle.kmips(W.U, W.P, W.k)
+    out = []
+    for order in (True, False):
+        with rkm.Context(prec, seed_order=order) as ctx:
+            tau, tid, topk = ctx.thresholds(dev(W.U), dev(W.P), W.k, want_topk=True)
+            st = ctx.stats()
+            out.append((tau.cpu().numpy(), tid.cpu().numpy(), topk.cpu().numpy()))
+            assert st["threshold_launches"] == (2 if order else 1)
+            # the seed pass computes n x 2048 products of its own
+            assert 0 < st["threshold_pairs"] < W.n * W.m + (W.n * 2048 if order else 0)
+    for tau, tid, topk in out:
+        np.testing.assert_array_equal(tau.view(np.uint64), tau_o.view(np.uint64))
+        np.testing.assert_array_equal(tid, tid_o)
+        np.testing.assert_array_equal(topk, topk_o)
+
+
 @pytest.mark.parametrize("prec", PRECISIONS)
 def test_filter_on_and_off_agree(rkm, prec):
     W = workloads.mf(30_000, 20_000, 32, 10, 20, seed=5)
