@@ -419,7 +419,7 @@ def run_ours(args, rank, local, world):
         e2e_s = max_over_ranks(statistics.mean(ts), world)
         e2e = {"value": world * pairs / e2e_s, "unit": UNIT, "ms_per_step": 1000 * e2e_s,
                "h2d_bytes_per_step": int(W.U.nbytes + W.P.nbytes), "d2h_bytes_per_step": int(8 * W.N),
-               "api": "rkm_topn_host"}
+               "api": "rkm_topn_host", "phase_ms_last_step": ctx.stats()["phase_ms"]}
     ctx.close()
 
     # The same inputs through the other precision paths: identical integer results (asserted)

@@ -121,6 +121,7 @@ enum {
     RKM_PHASE_COUNT = 4,     /* K5: counting product + classification              */
     RKM_PHASE_BAND = 5,      /* K6: exact rescoring of band pairs                  */
     RKM_PHASE_TOPN = 6,      /* K7: top-N select and the filter cut                */
+    RKM_PHASE_TRANSFER = 7,  /* host<->device copies of rkm_topn_host              */
     RKM_PHASES = 8
 };
 

@@ -58,11 +58,11 @@ class Stats(ctypes.Structure):
                 ("kernel_launches", ctypes.c_uint64), ("threshold_launches", ctypes.c_uint64),
                 ("phase_ms", ctypes.c_double * 8), ("threshold_pairs", ctypes.c_uint64)]
 
-    PHASES = ("prep", "threshold", "exact", "bounds", "count", "band", "topn", "unused")
+    PHASES = ("prep", "threshold", "exact", "bounds", "count", "band", "topn", "transfer")
 
     def as_dict(self) -> dict:
         out = {f: getattr(self, f) for f, _ in self._fields_ if f != "phase_ms"}
-        out["phase_ms"] = {name: self.phase_ms[i] for i, name in enumerate(self.PHASES[:7])}
+        out["phase_ms"] = {name: self.phase_ms[i] for i, name in enumerate(self.PHASES)}
         return out
 
 

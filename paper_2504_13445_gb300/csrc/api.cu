@@ -277,7 +277,7 @@ struct CtxLock {
 // Names of the phases in NVTX ranges (indices RKM_PHASE_*).
 const char* const PHASE_NAMES[RKM_PHASES] = {"rkm prep (K1)",   "rkm threshold (K2)", "rkm exact tau (K3)",
                                              "rkm bounds (K4)", "rkm count (K5)",     "rkm band (K6)",
-                                             "rkm top-N (K7)",  "rkm other"};
+                                             "rkm top-N (K7)",  "rkm host copies"};
 
 // One phase of a call: an NVTX range on the host thread (seen by Nsight tools when they are
 // attached; a no-op otherwise), and CUDA events around it on the call's stream when
@@ -1305,12 +1305,19 @@ rkm_status rkm_topn_host(rkm_ctx* c, const float* U, int64_t n, int64_t ldu, con
     TRY(c->ensure(c->h_P, std::max<int64_t>(m * ldp, 1), &dP));
     TRY(c->ensure(c->h_ids, N, &dids));
     TRY(c->ensure(c->h_sc, N, &dsc));
-    if (n > 0) CUDA_TRY(cudaMemcpyAsync(dU, U, n * ldu * sizeof(float), cudaMemcpyHostToDevice, s));
-    if (m > 0) CUDA_TRY(cudaMemcpyAsync(dP, P, m * ldp * sizeof(float), cudaMemcpyHostToDevice, s));
+    {
+        Phase ph(c, s, RKM_PHASE_TRANSFER);
+        if (n > 0) CUDA_TRY(cudaMemcpyAsync(dU, U, n * ldu * sizeof(float), cudaMemcpyHostToDevice, s));
+        if (m > 0) CUDA_TRY(cudaMemcpyAsync(dP, P, m * ldp * sizeof(float), cudaMemcpyHostToDevice, s));
+    }
     TRY(rkm_topn(c, dU, n, ldu, dP, m, ldp, d, k, N, dids, dsc, nullptr, nullptr, stream));
-    CUDA_TRY(cudaMemcpyAsync(ids, dids, N * sizeof(int32_t), cudaMemcpyDeviceToHost, s));
-    CUDA_TRY(cudaMemcpyAsync(top_scores, dsc, N * sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+    {
+        Phase ph(c, s, RKM_PHASE_TRANSFER);
+        CUDA_TRY(cudaMemcpyAsync(ids, dids, N * sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+        CUDA_TRY(cudaMemcpyAsync(top_scores, dsc, N * sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+    }
     CUDA_TRY(cudaStreamSynchronize(s));
+    collect_phases(c);
     return RKM_OK;
 }
 
