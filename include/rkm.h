@@ -27,8 +27,9 @@
  *    "host" are ordinary host memory.
  *  - `stream` is a cudaStream_t passed as void* (NULL = legacy default
  *    stream).  Every call enqueues its kernels on that stream and returns
- *    after its results are complete (each call reads back a device status
- *    word, so it synchronises `stream` once, or twice after a retry).
+ *    after its results are complete: it reads back a device status word
+ *    after each pass (the thresholds, the counting pass, each retry), so it
+ *    synchronises `stream` a few times.
  *  - The context owns its scratch memory (device workspace grown on demand
  *    and kept until rkm_destroy).  Calls on one context are thread-safe: a
  *    mutex inside the context serialises calls made from several host

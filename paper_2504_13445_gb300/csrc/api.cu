@@ -645,7 +645,10 @@ void threshold_exact(rkm_ctx* c, const float* U, int64_t ldu, const float* P, in
 // 2M x 500K, d = 128, the products computed fell from 59 % to 52 % of n*m and the threshold
 // phase from 116 to 104 ms; at 500K x 100K, d = 64, where the epilogue bounds the kernel, the
 // phase grew from 7.9 to 8.9 ms.
-constexpr int64_t SEED_TILES = 8;
+#ifndef RKM_SEED_TILES
+#define RKM_SEED_TILES 8
+#endif
+constexpr int64_t SEED_TILES = RKM_SEED_TILES;
 
 rkm_status threshold_seed_order(rkm_ctx* c, const PathShape& ps, const float* U, int64_t n, int64_t ldu, int d,
                                 const RowPrep& up, const ItemSide& it, ThrPlan* pl, cudaStream_t s) {
