@@ -820,61 +820,64 @@ __global__ void __launch_bounds__(tc_threads(NG), 1)
             const int pos0 = cur.T * BI_TC + cg;
             const uint32_t tb = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)h * BI_TC + cg;
             uint32_t ra[32], rb[32];
-#ifdef RKM_PAIR_VOTE_COUNT
+            if constexpr (NG == 2) {
+                // One vote per 64-column pair (both chunks in flight), as in the threshold
+                // epilogue: measured 8 % shorter counting phase at d = 128.  The four-group
+                // kernel keeps one vote per chunk: with both chunks live its registers spill.
 #pragma unroll 1
-            for (int c0 = 0; c0 < CW; c0 += 64) {
-                __syncwarp();
-                tmem_ld32_issue(tb + c0, ra);
-                tmem_ld32_issue(tb + c0 + 32, rb);
+                for (int c0 = 0; c0 < CW; c0 += 64) {
+                    __syncwarp();
+                    tmem_ld32_issue(tb + c0, ra);
+                    tmem_ld32_issue(tb + c0 + 32, rb);
+                    tmem_wait_bind(ra);
+                    tmem_wait_bind(rb);
+                    float va[32], vb[32];
+                    as_floats(ra, va);
+                    as_floats(rb, vb);
+                    if constexpr (FP8) {
+                        scale_values(va, f);
+                        scale_values(vb, f);
+                    }
+                    float ga[4], gb[4];
+                    group_max8(va, ga);
+                    group_max8(vb, gb);
+                    const float mx = fmaxf(fmax3f(ga[0], ga[1], fmaxf(ga[2], ga[3])),
+                                           fmax3f(gb[0], gb[1], fmaxf(gb[2], gb[3])));
+                    if (__any_sync(0xffffffffu, active && mx >= lo_t)) {
+                        count_chunk(va, active, c0, pos0 + c0, hot.m, hi_t, lo_t, cw, u_orig, hot.band,
+                                    hot.band_cap, hot.st);
+                        count_chunk(vb, active, c0 + 32, pos0 + c0 + 32, hot.m, hi_t, lo_t, cw, u_orig, hot.band,
+                                    hot.band_cap, hot.st);
+                    }
+                }
+            } else {
+                tmem_ld32_issue(tb, ra);
                 tmem_wait_bind(ra);
-                tmem_wait_bind(rb);
-                float va[32], vb[32];
-                as_floats(ra, va);
-                as_floats(rb, vb);
-                if constexpr (FP8) {
-                    scale_values(va, f);
-                    scale_values(vb, f);
-                }
-                float ga[4], gb[4];
-                group_max8(va, ga);
-                group_max8(vb, gb);
-                const float mx = fmaxf(fmax3f(ga[0], ga[1], fmaxf(ga[2], ga[3])),
-                                       fmax3f(gb[0], gb[1], fmaxf(gb[2], gb[3])));
-                if (__any_sync(0xffffffffu, active && mx >= lo_t)) {
-                    count_chunk(va, active, c0, pos0 + c0, hot.m, hi_t, lo_t, cw, u_orig, hot.band, hot.band_cap,
-                                hot.st);
-                    count_chunk(vb, active, c0 + 32, pos0 + c0 + 32, hot.m, hi_t, lo_t, cw, u_orig, hot.band,
-                                hot.band_cap, hot.st);
-                }
-            }
-#else
-            tmem_ld32_issue(tb, ra);
-            tmem_wait_bind(ra);
 #pragma unroll 1
-            for (int c0 = 0; c0 < CW; c0 += 64) {
-                __syncwarp();
-                tmem_ld32_issue(tb + c0 + 32, rb);
-                {
-                    float v[32];
-                    as_floats(ra, v);
-                    if constexpr (FP8) scale_values(v, f);
-                    count_chunk(v, active, c0, pos0 + c0, hot.m, hi_t, lo_t, cw, u_orig, hot.band, hot.band_cap,
-                                hot.st);
+                for (int c0 = 0; c0 < CW; c0 += 64) {
+                    __syncwarp();
+                    tmem_ld32_issue(tb + c0 + 32, rb);
+                    {
+                        float v[32];
+                        as_floats(ra, v);
+                        if constexpr (FP8) scale_values(v, f);
+                        count_chunk(v, active, c0, pos0 + c0, hot.m, hi_t, lo_t, cw, u_orig, hot.band,
+                                    hot.band_cap, hot.st);
+                    }
+                    __syncwarp();
+                    tmem_wait_bind(rb);
+                    if (c0 + 64 < CW) tmem_ld32_issue(tb + c0 + 64, ra);
+                    {
+                        float v[32];
+                        as_floats(rb, v);
+                        if constexpr (FP8) scale_values(v, f);
+                        count_chunk(v, active, c0 + 32, pos0 + c0 + 32, hot.m, hi_t, lo_t, cw, u_orig, hot.band,
+                                    hot.band_cap, hot.st);
+                    }
+                    __syncwarp();
+                    if (c0 + 64 < CW) tmem_wait_bind(ra);
                 }
-                __syncwarp();
-                tmem_wait_bind(rb);
-                if (c0 + 64 < CW) tmem_ld32_issue(tb + c0 + 64, ra);
-                {
-                    float v[32];
-                    as_floats(rb, v);
-                    if constexpr (FP8) scale_values(v, f);
-                    count_chunk(v, active, c0 + 32, pos0 + c0 + 32, hot.m, hi_t, lo_t, cw, u_orig, hot.band,
-                                hot.band_cap, hot.st);
-                }
-                __syncwarp();
-                if (c0 + 64 < CW) tmem_wait_bind(ra);
             }
-#endif
             tc_fence_before();
             __syncwarp();
             if (lane == 0) mbar_arrive(&B->tempty[h]);
