@@ -239,6 +239,9 @@ RKM_API rkm_status rkm_item_bounds(rkm_ctx* ctx, const float* U, int64_t n, int6
  *                    must hold for every pair.
  *   U: device n x d (stride ldu), 0 <= n <= 65536; P: device m x d (stride ldp),
  *   0 <= m <= 2^20; v, E: device [n * ldo] float, ldo >= m.  RKM_EINVAL on the FP32 path.
+ * The product kernels skip 64-column blocks of a tile on the row maximum that the TMEM load
+ * instruction returns with the values (tcgen05.ld with .red.max); this call checks that
+ * maximum against the values it loads and returns RKM_EINTERNAL if they ever differ.
  */
 RKM_API rkm_status rkm_debug_products(rkm_ctx* ctx, const float* U, int64_t n, int64_t ldu,
                                       const float* P, int64_t m, int64_t ldp, int d,

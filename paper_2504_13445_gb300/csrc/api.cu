@@ -1399,6 +1399,8 @@ rkm_status rkm_debug_products(rkm_ctx* c, const float* U, int64_t n, int64_t ldu
     a.st = c->st;
     launch_products_tc(a, &tm.a, &tm.b, ps.fp8, s);
     TRY(read_status(c, s));
+    if (c->st_host->internal_error)
+        return fail(RKM_EINTERNAL, "rkm_debug_products: a TMEM load's row maximum differs from its values");
     return RKM_OK;
 }
 

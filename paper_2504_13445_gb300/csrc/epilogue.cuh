@@ -214,10 +214,11 @@ __device__ __forceinline__ unsigned hit_mask(const float (&v)[32], const float (
     return mask;
 }
 
-// Threshold-pass epilogue of one 32-column chunk.  Must be called by all 32 lanes of the
-// warp: the fast path is one maximum tree and one vote; 8-column groups in which some lane
-// reaches its threshold are compared element by element, and the hits are inserted one by
-// one through a single call site.  `active` masks lanes without a valid user.
+// Threshold-pass epilogue of one 32-column chunk, called when the pair vote of the product
+// kernel found a value reaching some lane's threshold.  Must be called by all 32 lanes of the
+// warp: a maximum tree and a vote skip a chunk without hits; 8-column groups in which some
+// lane reaches its threshold are compared element by element, and the hits are inserted one
+// by one through a single call site.  `active` masks lanes without a valid user.
 __device__ __forceinline__ void sel_chunk(const float (&v)[32], bool active, int pos0, int64_t m,
                                           float E, SelState& s, Cand* mycand, int cap, float* heap,
                                           int t, int k, DevStatus* st) {

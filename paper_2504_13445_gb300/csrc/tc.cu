@@ -468,31 +468,30 @@ __global__ void __launch_bounds__(tc_threads(NG), 1)
                 }
                 s.thr = __fsub_rd(sel_bound(s), E);
                 uint32_t ra[32], rb[32];
-                // Both 32-column chunks of a 64-column pair in flight, one vote for the pair: the
-                // common case (no value of the pair reaches its row's threshold) costs two max
-                // trees, one vote and one branch.  Measured on GB300 against one vote per chunk
-                // with the next chunk's load overlapping the current one: threshold phase 4-5 %
-                // shorter at d = 64 and d = 128.
+                // Both 32-column chunks of a 64-column pair in flight, one vote for the pair.  The
+                // loads (tcgen05.ld with .red.max, an sm_103a form) return each chunk's row
+                // maximum with its values, so the common case (no value of the pair reaches its
+                // row's threshold) costs one maximum, one vote and one branch, with no reduction
+                // tree.  Measured on GB300 against max trees over the loaded values: threshold
+                // phase 8 % shorter at d = 64 and d = 128.  The FP8 descale f is a positive power
+                // of two and rounding is monotone, so max(v f) = max(v) f.
 #pragma unroll 1
                 for (int c0 = 0; c0 < CW; c0 += 64) {
                     __syncwarp();
-                    tmem_ld32_issue(tb + c0, ra);
-                    tmem_ld32_issue(tb + c0 + 32, rb);
-                    tmem_wait_bind(ra);
-                    tmem_wait_bind(rb);
-                    float va[32], vb[32];
-                    as_floats(ra, va);
-                    as_floats(rb, vb);
-                    if constexpr (FP8) {
-                        scale_values(va, f);
-                        scale_values(vb, f);
-                    }
-                    float ga[4], gb[4];
-                    group_max8(va, ga);
-                    group_max8(vb, gb);
-                    const float mx = fmaxf(fmax3f(ga[0], ga[1], fmaxf(ga[2], ga[3])),
-                                           fmax3f(gb[0], gb[1], fmaxf(gb[2], gb[3])));
+                    float ma, mb;
+                    tmem_ld32_max_issue(tb + c0, ra, ma);
+                    tmem_ld32_max_issue(tb + c0 + 32, rb, mb);
+                    tmem_wait_bind_max(ra, ma);
+                    tmem_wait_bind_max(rb, mb);
+                    const float mx = FP8 ? fmaxf(ma, mb) * f : fmaxf(ma, mb);
                     if (__any_sync(0xffffffffu, active && mx >= s.thr)) {
+                        float va[32], vb[32];
+                        as_floats(ra, va);
+                        as_floats(rb, vb);
+                        if constexpr (FP8) {
+                            scale_values(va, f);
+                            scale_values(vb, f);
+                        }
                         sel_chunk(va, active, it * BI_TC + cg + c0, a.m, E, s, mycand, a.cap, heap, r, a.k, a.st);
                         sel_chunk(vb, active, it * BI_TC + cg + c0 + 32, a.m, E, s, mycand, a.cap, heap, r, a.k,
                                   a.st);
@@ -820,17 +819,18 @@ __global__ void __launch_bounds__(tc_threads(NG), 1)
             const int pos0 = cur.T * BI_TC + cg;
             const uint32_t tb = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)h * BI_TC + cg;
             uint32_t ra[32], rb[32];
-            if constexpr (NG == 2) {
-                // One vote per 64-column pair (both chunks in flight), as in the threshold
-                // epilogue: measured 8 % shorter counting phase at d = 128.  The four-group
-                // kernel keeps one vote per chunk: with both chunks live its registers spill.
+            // One vote per 64-column pair on the row maxima the two loads return, as in the
+            // threshold epilogue.
 #pragma unroll 1
-                for (int c0 = 0; c0 < CW; c0 += 64) {
-                    __syncwarp();
-                    tmem_ld32_issue(tb + c0, ra);
-                    tmem_ld32_issue(tb + c0 + 32, rb);
-                    tmem_wait_bind(ra);
-                    tmem_wait_bind(rb);
+            for (int c0 = 0; c0 < CW; c0 += 64) {
+                __syncwarp();
+                float ma, mb;
+                tmem_ld32_max_issue(tb + c0, ra, ma);
+                tmem_ld32_max_issue(tb + c0 + 32, rb, mb);
+                tmem_wait_bind_max(ra, ma);
+                tmem_wait_bind_max(rb, mb);
+                const float mx = FP8 ? fmaxf(ma, mb) * f : fmaxf(ma, mb);
+                if (__any_sync(0xffffffffu, active && mx >= lo_t)) {
                     float va[32], vb[32];
                     as_floats(ra, va);
                     as_floats(rb, vb);
@@ -838,44 +838,10 @@ __global__ void __launch_bounds__(tc_threads(NG), 1)
                         scale_values(va, f);
                         scale_values(vb, f);
                     }
-                    float ga[4], gb[4];
-                    group_max8(va, ga);
-                    group_max8(vb, gb);
-                    const float mx = fmaxf(fmax3f(ga[0], ga[1], fmaxf(ga[2], ga[3])),
-                                           fmax3f(gb[0], gb[1], fmaxf(gb[2], gb[3])));
-                    if (__any_sync(0xffffffffu, active && mx >= lo_t)) {
-                        count_chunk(va, active, c0, pos0 + c0, hot.m, hi_t, lo_t, cw, u_orig, hot.band,
-                                    hot.band_cap, hot.st);
-                        count_chunk(vb, active, c0 + 32, pos0 + c0 + 32, hot.m, hi_t, lo_t, cw, u_orig, hot.band,
-                                    hot.band_cap, hot.st);
-                    }
-                }
-            } else {
-                tmem_ld32_issue(tb, ra);
-                tmem_wait_bind(ra);
-#pragma unroll 1
-                for (int c0 = 0; c0 < CW; c0 += 64) {
-                    __syncwarp();
-                    tmem_ld32_issue(tb + c0 + 32, rb);
-                    {
-                        float v[32];
-                        as_floats(ra, v);
-                        if constexpr (FP8) scale_values(v, f);
-                        count_chunk(v, active, c0, pos0 + c0, hot.m, hi_t, lo_t, cw, u_orig, hot.band,
-                                    hot.band_cap, hot.st);
-                    }
-                    __syncwarp();
-                    tmem_wait_bind(rb);
-                    if (c0 + 64 < CW) tmem_ld32_issue(tb + c0 + 64, ra);
-                    {
-                        float v[32];
-                        as_floats(rb, v);
-                        if constexpr (FP8) scale_values(v, f);
-                        count_chunk(v, active, c0 + 32, pos0 + c0 + 32, hot.m, hi_t, lo_t, cw, u_orig, hot.band,
-                                    hot.band_cap, hot.st);
-                    }
-                    __syncwarp();
-                    if (c0 + 64 < CW) tmem_wait_bind(ra);
+                    count_chunk(va, active, c0, pos0 + c0, hot.m, hi_t, lo_t, cw, u_orig, hot.band,
+                                hot.band_cap, hot.st);
+                    count_chunk(vb, active, c0 + 32, pos0 + c0 + 32, hot.m, hi_t, lo_t, cw, u_orig, hot.band,
+                                hot.band_cap, hot.st);
                 }
             }
             tc_fence_before();
@@ -987,9 +953,18 @@ __global__ void __launch_bounds__(128, 1)
         const float E = active ? err_bound(a.cacc, a.eabs, a.unrm[u], a.unhat[u], a.udel[u], thm, tdl) : 0.f;
         const float f = (FP8 && active) ? pow2i(fp8_exp(a.uexp[u]) + a.texp[it] - 16) : 1.f;
         for (int c0 = 0; c0 < BI_TC; c0 += 32) {
-            float v[32];
+            uint32_t rv[32];
+            float v[32], mx;
             __syncwarp();
-            tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + c0, v);
+            tmem_ld32_max_issue(tmem + ((uint32_t)(warp * 32) << 16) + c0, rv, mx);
+            tmem_wait_bind_max(rv, mx);
+            as_floats(rv, v);
+            // The product kernels vote on the maximum returned by the load itself: check it
+            // against the loaded values (a mismatch makes the call return RKM_EINTERNAL).
+            float ref = v[0];
+#pragma unroll
+            for (int j = 1; j < 32; ++j) ref = fmaxf(ref, v[j]);
+            if (!(mx == ref)) a.st->internal_error = 1u;
             if (!active) continue;
 #pragma unroll
             for (int j = 0; j < 32; ++j) {
