@@ -159,7 +159,7 @@ def measured_peaks() -> dict:
 # the figure is their mean, like the kernel time of the roofline), keyed by a hash of the
 # kernel sources: when the kernel changes, the counters no longer apply (None).
 THRESHOLD_TRAFFIC = {
-    "918a35a0f85056a2d1d2018537535b15ccd1f996ac0c259c4fcfb7f254296413": {"mf-2m-k10": 5.08e9},
+    "5e94e6ae1c4c4eadd13e89eec5a3cec0483326071ca6273ee93fd0faab5a9de7": {"mf-2m-k10": 5.11e+09, "mf-500k": 5.75e+08},
 }
 KERNEL_SOURCES = ['tc.cu', 'epilogue.cuh', 'tc_ptx.cuh', 'common.cuh']
 
@@ -521,7 +521,9 @@ def compare_paths(args, rkm, U, P, W, ref_out, local, main_ms, flush):
         counting = st["pairs_evaluated"] - st["threshold_pairs"]
         out[prec] = {"ms_per_step": ms, "identical_results": True,
                      "phase_ms": st["phase_ms"], "candidates_per_user": st["candidates"] / W.n,
-                     "band_hit_fraction": st["band_pairs"] / max(1, counting) if args.scores == "count" else None}
+                     "band_hit_fraction": st["band_pairs"] / max(1, counting) if args.scores == "count" else None,
+                     "band_pairs": st["band_pairs"], "counting_pairs": counting,
+                     "threshold_pairs": st["threshold_pairs"], "retries": st["retries"]}
     if "fp32" in out and args.precision != "fp32":
         out["speedup_vs_fp32"] = {p: out["fp32"]["ms_per_step"] / v["ms_per_step"]
                                   for p, v in out.items() if p in ("bf16", "fp8")}
