@@ -861,6 +861,16 @@ void scatter_i32(const int* src, const int* perm, int64_t count, int* dst, cudaS
 
 rkm_status ensure_band(rkm_ctx* c, int2** band) { return c->ensure(c->band, c->band_cap, band); }
 
+// The band queue's size after an overflow: twice the old one, or the pairs the call pushed
+// plus an eighth.  The margin matters for later calls on the same inputs: the bucket sorts
+// do not fix the order of users (or items) within a bucket, so which users share the last
+// user tile of a counting unit, and with it the band of a repeated call, varies by a few
+// pairs in 10^4.
+int64_t grown_band_cap(const rkm_ctx* c) {
+    const int64_t pushed = (int64_t)c->st_host->band_count;
+    return std::min<int64_t>((int64_t)UINT32_MAX - 1, std::max<int64_t>(c->band_cap * 2, pushed + pushed / 8 + 1024));
+}
+
 // Initial capacities of a call: the option (or a default sized from n and k), or the
 // capacity a previous call on this context grew to, whichever is larger.
 void init_caps(rkm_ctx* c, int64_t n, int k) {
@@ -929,8 +939,7 @@ rkm_status rkm::query_resident(rkm_ctx* c, const rkm_ctx* r, const float* Q, int
         TRY(read_status(c, s));
         if (!c->st_host->band_overflow) break;
         if (attempt >= 3) return fail(RKM_EOVERFLOW, "band queue overflowed");
-        c->band_cap = std::min<int64_t>((int64_t)UINT32_MAX - 1,
-                                        std::max<int64_t>(c->band_cap * 2, (int64_t)c->st_host->band_count + 1024));
+        c->band_cap = grown_band_cap(c);
         c->stats.retries++;
         CUDA_TRY(cudaMemsetAsync(&c->st->band_overflow, 0, sizeof(unsigned), s));
     }
@@ -1123,8 +1132,7 @@ rkm_status count_enqueue(rkm_ctx* c, const PathShape& ps, int64_t n, const ItemS
 // Grow the band queue after an overflow.
 rkm_status grow_band(rkm_ctx* c, int attempt) {
     if (attempt >= 3) return fail(RKM_EOVERFLOW, "band queue (%lld pairs) overflowed", (long long)c->band_cap);
-    c->band_cap = std::min<int64_t>((int64_t)UINT32_MAX - 1,
-                                    std::max<int64_t>(c->band_cap * 2, (int64_t)c->st_host->band_count + 1024));
+    c->band_cap = grown_band_cap(c);
     c->stats.retries++;
     return RKM_OK;
 }

@@ -393,6 +393,8 @@ __global__ void __launch_bounds__(tc_threads(NG), 1)
             s.defer = 1;
             s.mark = 0;
             bool warm = false;  // warm start done for this unit
+            int fb = item_tiles;       // first tile after the last searched one whose
+            float bnd_fb = -INFINITY;  // ||u|| max||p|| is below bnd_fb (see the stop below)
             // Packed row u holds original user uo; a seed bound of tau_u (from a pass over the
             // highest-norm items) starts the selector above -inf.
             const int64_t uo = (active && a.uperm) ? (int64_t)a.uperm[u] : u;
@@ -507,16 +509,25 @@ __global__ void __launch_bounds__(tc_threads(NG), 1)
                 // so once ||u|| max||p|| of a tile (rounded up) is below a lower bound of tau_u,
                 // no item of that tile or any later one can reach tau_u or tie it.  Publish how
                 // many leading tiles this warp's users still need.
+                // The first tile below a bound moves back as the bound grows, so the search
+                // is skipped while the bound is unchanged and narrowed to [it + 1, fb] when it
+                // grew; the other groups' bounds can make it drop (a group that has moved on
+                // publishes for its next unit), and then the whole rest is searched.
                 {
                     const float bnd = sel_bound(s);
                     int need = 0;
                     if (active) {
-                        int lo = it + 1, hi = item_tiles;  // first tile below the bound
-                        while (lo < hi) {
-                            const int mid = (lo + hi) >> 1;
-                            if (__fmul_ru(un, a.tmax[mid]) < bnd) hi = mid; else lo = mid + 1;
+                        if (bnd != bnd_fb || fb < it + 1) {
+                            int lo = it + 1, hi = item_tiles;  // first tile below the bound
+                            if (bnd >= bnd_fb && fb < hi) hi = fb > lo ? fb : lo;
+                            while (lo < hi) {
+                                const int mid = (lo + hi) >> 1;
+                                if (__fmul_ru(un, a.tmax[mid]) < bnd) hi = mid; else lo = mid + 1;
+                            }
+                            fb = lo;
+                            bnd_fb = bnd;
                         }
-                        need = lo;
+                        need = fb;
                     }
                     need = __reduce_max_sync(0xffffffffu, need);
                     if (lane == 0)
