@@ -199,6 +199,21 @@ def test_small_capacity_retries(rkm, prec):
         full_check(ctx, W.U, W.P, W.k, W.N)
 
 
+def test_grown_band_queue_holds_on_repeat_calls(rkm):
+    # The first call overflows a 64-pair band queue and grows it; repeated calls on the same
+    # inputs push a slightly different band (the order of users within a ratio bucket is not
+    # fixed), and the grown queue keeps a margin for that: no further retries, same results.
+    W = workloads.mf(20_000, 8_000, 64, 10, 20, seed=33)
+    with rkm.Context("bf16", band_capacity=64) as ctx:
+        first = [t.cpu().numpy() for t in ctx.topn(dev(W.U), dev(W.P), W.k, W.N, return_thresholds=True)]
+        assert ctx.stats()["retries"] > 0
+        for _ in range(3):
+            again = [t.cpu().numpy() for t in ctx.topn(dev(W.U), dev(W.P), W.k, W.N, return_thresholds=True)]
+            assert ctx.stats()["retries"] == 0
+            for x, y in zip(first, again):
+                np.testing.assert_array_equal(x, y)
+
+
 def test_host_buffers_entry_point(rkm):
     W = workloads.make("plain-2k")
     tau_o, tid_o, topk_o = oracle.kmips(W.U, W.P, W.k)
